@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Isochrone query throughput on one or more GB300s.
+
+One step = one batch of k isochrone queries through the whole hot path
+(upward CH search, persistent level sweep, isochrone-edge emission, per-query
+sort) on the synthetic 4,243 x 4,243 road-like grid (18,003,049 vertices).
+Default workload: 64 sources per sweep with limits drawn uniformly from
+[3,600, 72,000], CUDA-graph replay.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N --steps K --warmup W] [--workload NAME] [--impl ours|reference]
+
+With N > 1 (torchrun) every rank holds a replica of the graph and answers its
+own batches; value = queries answered by all ranks / slowest rank's time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    # 18M-vertex graph, 64 sources per sweep, uneven limits
+    "grid18m_k64": dict(graph="grid18m", k=64, tau=("uniform", 3600, 72000)),
+    # 18M-vertex graph, 16 sources per sweep, shared limit
+    "grid18m_k16": dict(graph="grid18m", k=16, tau=("fixed", 36000)),
+    # 18M-vertex graph, one source per launch
+    "grid18m_k1": dict(graph="grid18m", k=1, tau=("uniform", 3600, 72000)),
+    "grid1k_k1": dict(graph="grid1k", k=1, tau=("choice", (2000, 10000, 50000))),
+    "grid1k_k16": dict(graph="grid1k", k=16, tau=("choice", (2000, 10000, 50000))),
+    "grid1k_k64": dict(graph="grid1k", k=64, tau=("uniform", 2000, 50000)),
+}
+METRIC = "isochrone queries/s on 18M-vertex graph (1 GB300); sweep HBM GB/s vs peak; p99 ms"
+CACHE = os.path.join(ROOT, "paper_1512_09090_gb300", "_cache")
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def draw_taus(spec, k, seed):
+    from paper_1512_09090_gb300 import synth
+    kind = spec[0]
+    if kind == "fixed":
+        return np.full(k, spec[1], np.int32)
+    if kind == "uniform":
+        return synth.draw_taus_uniform(k, spec[1], spec[2], seed)
+    rng = np.random.default_rng(seed)
+    return np.asarray(spec[1], np.int32)[rng.integers(0, len(spec[1]), size=k)]
+
+
+def load_graph_and_ch(name):
+    """Generate the graph and build (or load a cached) contraction hierarchy."""
+    import paper_1512_09090_gb300 as P
+    from paper_1512_09090_gb300 import synth
+    t0 = time.time()
+    g = synth.workload_graph(name)
+    log(f"[bench] graph {name}: n={g.n} m={g.m} ({time.time() - t0:.1f}s)")
+    h = hashlib.sha1(json.dumps(synth.WORKLOADS[name], sort_keys=True).encode())
+    with open(os.path.join(ROOT, "paper_1512_09090_gb300", "csrc", "ch.cpp"), "rb") as f:
+        h.update(f.read())
+    path = os.path.join(CACHE, f"{name}-{h.hexdigest()[:12]}.ch")
+    if os.path.exists(path):
+        try:
+            ch = P.iso_load_ch(path)
+            log(f"[bench] CH loaded from cache {os.path.basename(path)}")
+            return g, ch
+        except Exception as e:  # rebuild below
+            log(f"[bench] cache unreadable ({e}); rebuilding")
+    t0 = time.time()
+    ch = P.iso_build_ch(g.n, g.tail, g.head, g.weight)
+    log(f"[bench] CH built in {time.time() - t0:.1f}s: {ch.stats()}")
+    try:
+        os.makedirs(CACHE, exist_ok=True)
+        tmp = path + f".tmp{os.getpid()}"
+        ch.save(tmp)
+        os.replace(tmp, path)
+    except OSError as e:
+        log(f"[bench] could not cache the CH: {e}")
+    return g, ch
+
+
+def sweep_bytes(A, k, write_all=False):
+    """Algorithmic bytes one sweep of k lanes must move."""
+    n = A["perm"].shape[0]
+    lo = A["level_off"]
+    n_low = int(lo[-1] - lo[-2])                 # lowest level: rows not stored
+    n_hi = n if write_all else n - n_low
+    n_src = int(np.unique(A["down_src"]).shape[0])  # rows read at least once
+    m_down = int(A["down_src"].shape[0])
+    mask_b = 1 if k <= 8 else k // 8
+    return dict(offsets=4 * (n + 1), arcs=8 * m_down, d_write=4 * k * n_hi, d_read=4 * k * n_src,
+                mask_write=mask_b * n, upflag_read=n, levels=4 * (lo.shape[0]))
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(g, spec, k_hint, budget_s=15.0):
+    """The CPU oracle (Dijkstra stopped at tau + full arc scan) on a bounded
+    sample of the same workload, all host cores."""
+    import oracle
+    from paper_1512_09090_gb300 import synth
+    cores = os.cpu_count() or 1
+    srcs = synth.draw_sources(g, 1, 9001)
+    taus = draw_taus(spec["tau"], 1, 9002)
+    t0 = time.perf_counter()
+    oracle.query_batch(g.n, g.tail, g.head, g.weight, srcs, taus, threads=1)
+    t1 = max(time.perf_counter() - t0, 1e-3)
+    q = int(max(cores, min(4 * cores * max(1, int(budget_s / (t1 * 2))), 4096)))
+    q = max(cores, min(q, int(cores * budget_s / t1)))
+    srcs = synth.draw_sources(g, q, 9003)
+    taus = draw_taus(spec["tau"], q, 9004)
+    t0 = time.perf_counter()
+    oracle.query_batch(g.n, g.tail, g.head, g.weight, srcs, taus, threads=cores)
+    el = time.perf_counter() - t0
+    return {"value": q / el, "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "sample": f"{q} queries of the same workload (one-query latency {t1 * 1e3:.0f} ms single-threaded), "
+                      f"{el:.1f}s wall"}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def run_reference(args, spec):
+    """The oracle as the reference arm: same workload, metric and unit, on host cores."""
+    from paper_1512_09090_gb300 import synth
+    import oracle
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    g = synth.workload_graph(spec["graph"])
+    cores = os.cpu_count() or 1
+    oracle.build()
+    per_step = max(1, min(spec["k"], cores))
+    for w in range(args.warmup):
+        s = synth.draw_sources(g, per_step, 500 + w)
+        oracle.query_batch(g.n, g.tail, g.head, g.weight, s, draw_taus(spec["tau"], per_step, 600 + w), threads=cores)
+    times = []
+    for i in range(args.steps):
+        s = synth.draw_sources(g, per_step, 700 + i)
+        t = draw_taus(spec["tau"], per_step, 800 + i)
+        t0 = time.perf_counter()
+        oracle.query_batch(g.n, g.tail, g.head, g.weight, s, t, threads=cores)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = per_step * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": {"workload": args.workload, "graph": spec["graph"], "queries_per_step":
+                                            per_step},
+            "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} queries per step x {args.steps} steps"},
+            "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="grid18m_k64", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tpv", type=int, default=0)
+    ap.add_argument("--fuse", type=int, default=0)
+    ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    spec = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, spec)
+
+    import torch
+    import paper_1512_09090_gb300 as P
+    from paper_1512_09090_gb300 import _build, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    _build.build()
+    g, ch = load_graph_and_ch(spec["graph"])
+    A = ch.arrays()
+    dg = P.iso_upload_graph(ch)
+    k = spec["k"]
+    opts = dict(use_cuda_graph=1)
+    if args.tpv:
+        opts["threads_per_vertex"] = args.tpv
+    if args.fuse:
+        opts["fuse_width"] = args.fuse
+    if args.ctas_per_sm:
+        opts["ctas_per_sm"] = args.ctas_per_sm
+    ws = P.Workspace(dg, k, **opts)
+    nb = 16
+    batches = []
+    for b in range(nb):
+        s = synth.draw_sources(g, k, 10_000 * (rank + 1) + b)
+        t = draw_taus(spec["tau"], k, 20_000 * (rank + 1) + b)
+        batches.append((torch.from_numpy(s).cuda(), torch.from_numpy(t).cuda(), s, t))
+    out_off = torch.zeros(k + 1, dtype=torch.int64, device="cuda")
+    out_arcs = torch.zeros(64 * 65536, dtype=torch.int32, device="cuda")
+
+    def step(i):
+        s, t, _, _ = batches[i % nb]
+        ws.submit(s, t)
+        ws.collect(out_arcs=out_arcs, out_offsets=out_off)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    sweep_ms, lat_ms = [], []
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ev0.record(ws.stream)
+        for i in range(args.steps):
+            t0 = time.perf_counter()
+            step(i)
+            lat_ms.append((time.perf_counter() - t0) * 1e3)
+            sweep_ms.append(ws.timings()["sweep"])
+        ev1.record(ws.stream)
+        torch.cuda.synchronize()
+    el_ms = ev0.elapsed_time(ev1)
+    if dist:
+        tt = torch.tensor([el_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        el_ms = float(tt.item())
+        dist.barrier()
+    value = world * k * args.steps / (el_ms / 1e3)
+
+    # end to end through the public call with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        pin_s = torch.empty(k, dtype=torch.int32, pin_memory=True)
+        pin_t = torch.empty(k, dtype=torch.int32, pin_memory=True)
+        pin_off = torch.empty(k + 1, dtype=torch.int64, pin_memory=True)
+        pin_arcs = torch.empty(64 * 65536, dtype=torch.int32, pin_memory=True)
+        hs, ht, ho, ha = pin_s.numpy(), pin_t.numpy(), pin_off.numpy(), pin_arcs.numpy()
+        d2h = 0
+        for i in range(args.warmup):
+            hs[:] = batches[i % nb][2]; ht[:] = batches[i % nb][3]
+            P.iso_query(dg, hs, ht, out_offsets=ho, out_arcs=ha, cap=ha.shape[0], **opts)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            hs[:] = batches[i % nb][2]; ht[:] = batches[i % nb][3]
+            P.iso_query(dg, hs, ht, out_offsets=ho, out_arcs=ha, cap=ha.shape[0], **opts)
+            d2h += int(ho[-1]) * 4 + (k + 1) * 8
+        e2e_s = time.perf_counter() - t0
+        if dist:
+            tt = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        e2e = {"value": world * k * args.steps / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": 2 * 4 * k,
+               "d2h_bytes_per_step": d2h // args.steps}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    bb = sweep_bytes(A, k)
+    alg = sum(bb.values())
+    sw = statistics.mean(sweep_ms)
+    peak, src = peaks()
+    achieved = alg / (sw / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None, "kernel": "k_sweep",
+            "alg_bytes_per_launch": alg, "peak_source": src, "sweep_ms": round(sw, 4)}
+    lat = sorted(lat_ms)
+    line = {"metric": METRIC, "value": round(value, 2), "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(el_ms / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": args.workload, "graph": spec["graph"], "n": g.n, "m": g.m,
+                       "m_down": int(A["down_src"].shape[0]), "levels": int(A["level_off"].shape[0] - 1),
+                       "queries_per_sweep": k, "tau": list(spec["tau"]), "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (distance rows " + f"{4 * k * g.n / 1e9:.2f} GB)",
+                       "opts": opts},
+            "roofline": roof,
+            "latency_ms": {"p50": round(lat[len(lat) // 2], 3), "p99": round(lat[min(len(lat) - 1,
+                                                                                     int(0.99 * len(lat)))], 3)},
+            "gpu_launches": 4 * args.steps, "e2e": e2e}
+    clocks = clk.summary()
+    if clocks:
+        line["clocks"] = clocks
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(g, spec, k)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

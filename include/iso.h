@@ -1,0 +1,195 @@
+/*
+ * iso.h -- C ABI of the GB300 isochrone library (libiso.so).
+ *
+ * An isochrone query (Baum, Buchhold, Dibbelt, Wagner, "Fast Computation of
+ * Isochrones in Road Networks", Section 3) takes a source s and a time limit
+ * tau and returns the isochrone edges: every arc (u,v) of the input graph with
+ * exactly one endpoint in range, where v is in range iff d(s,v) <= tau.
+ *
+ * The library answers it PHAST-style (Section 2): a contraction hierarchy (CH)
+ * is built once on the host (iso_build_ch); a query runs an upward CH search
+ * from s, then one sweep over all vertices in descending CH level in which each
+ * vertex takes the minimum over its incoming downward arcs, pruned at tau, and
+ * finally a pass that emits the arcs whose endpoints are on different sides of
+ * tau.  k queries share one sweep ("lanes").
+ *
+ * Conventions for every call:
+ *   - vertices are 0..n-1, arcs are identified by their input index 0..m-1;
+ *   - lengths and limits are int32 >= 0, in the same unit;
+ *   - a distance label is d(s,v) if v is in range and 0x7FFFFFFF otherwise;
+ *   - every call returns an ISO_* status; nothing throws across the ABI; the
+ *     calling thread's last error message is available from iso_last_error();
+ *   - objects (iso_ch, iso_graph, iso_workspace) are owned by the library and
+ *     released with the matching iso_free_* call; input arrays are borrowed
+ *     only for the duration of the call; output arrays belong to the caller.
+ */
+#ifndef ISO_H
+#define ISO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ISO_OK          0
+#define ISO_E_INVAL     1  /* bad argument (null pointer, id out of range, negative length/limit, ...) */
+#define ISO_E_NOMEM     2  /* host or device allocation failed */
+#define ISO_E_OVERFLOW  3  /* output capacity too small; offsets hold the sizes needed */
+#define ISO_E_CUDA      4  /* a CUDA runtime call or kernel launch failed */
+#define ISO_E_TIMEOUT   5  /* a device-side grid barrier gave up waiting; results are invalid */
+#define ISO_E_IO        6  /* file could not be read or written, or is not a CH file */
+#define ISO_E_NODEV     7  /* no usable CUDA device (the library never falls back to the CPU) */
+
+#define ISO_DIST_INF 0x7FFFFFFF
+
+typedef struct iso_ch iso_ch;               /* host contraction hierarchy */
+typedef struct iso_graph iso_graph;         /* device-resident copy of a CH */
+typedef struct iso_workspace iso_workspace; /* per-batch device buffers + stream state */
+
+/* ---------------------------------------------------------------------------
+ * Contraction hierarchy (Section 2: vertices are contracted in an order rank,
+ * shortcuts preserve distances, and levels satisfy l(v) = max(l(v), l(u)+1)
+ * for every neighbour v still present when u is contracted).
+ * ------------------------------------------------------------------------- */
+
+typedef struct {
+    int32_t threads;              /* host threads for contraction; 0 = all available */
+    int32_t witness_settle_limit; /* vertices a witness search may settle; 0 = default (400) */
+    int32_t priority_settle_limit;/* > 2: priorities count shortcuts with witness searches of
+                                     this many settled vertices; 0 = default: witnesses of at
+                                     most two arcs (cheaper, slightly larger hierarchy) */
+    int32_t reserved[5];          /* must be zero */
+} iso_ch_opts;
+
+typedef struct {
+    int32_t n;          /* vertices */
+    int32_t levels;     /* number of CH levels L */
+    int64_t m;          /* original arcs */
+    int64_t m_up;       /* arcs of the upward graph (original + shortcuts, rank increasing) */
+    int64_t m_down;     /* arcs of the downward graph (rank decreasing) */
+    int64_t shortcuts;  /* shortcut arcs added by contraction */
+    int32_t max_weight; /* largest input length */
+    int32_t max_level_width; /* vertices in the widest level */
+    double  build_seconds;
+} iso_ch_stats;
+
+/* Build a CH of the directed graph with n vertices and m arcs (tail[e] ->
+ * head[e], length weight[e]).  Arrays are host memory and are copied.
+ * Parallel arcs and self-loops are accepted.  Errors: ISO_E_INVAL for n <= 0,
+ * m < 0, null arrays with m > 0, endpoints outside [0,n), negative lengths, or
+ * a graph whose downward arc count exceeds 2^32-1; ISO_E_NOMEM. */
+int iso_build_ch(int32_t n, int64_t m, const int32_t* tail, const int32_t* head,
+                 const int32_t* weight, const iso_ch_opts* opts /* nullable */, iso_ch** out);
+
+int  iso_ch_info(const iso_ch* ch, iso_ch_stats* out);
+/* Write / read a CH in the library's own binary format (little-endian, with a
+ * magic header and sizes).  Loading validates sizes and ids; ISO_E_IO otherwise. */
+int  iso_save_ch(const iso_ch* ch, const char* path);
+int  iso_load_ch(const char* path, iso_ch** out);
+/* Read-only views of the CH arrays, valid until iso_free_ch.  Sweep order is
+ * descending level; level_off[j]..level_off[j+1] holds level L-1-j.  Downward
+ * arcs are listed at their head, upward arcs at their tail, original arcs at
+ * their tail; all vertex ids in the arrays are sweep positions. */
+typedef struct {
+    const int32_t* perm;      /* [n] sweep position -> original id */
+    const int32_t* pos;       /* [n] original id -> sweep position */
+    const int32_t* level_off; /* [L+1] */
+    const int64_t* down_off;  /* [n+1] */
+    const int32_t* down_src;  /* [m_down] */
+    const int32_t* down_w;    /* [m_down] */
+    const int64_t* up_off;    /* [n+1] */
+    const int32_t* up_dst;    /* [m_up] */
+    const int32_t* up_w;      /* [m_up] */
+    const int64_t* orig_off;  /* [n+1] */
+    const int32_t* orig_head; /* [m] */
+    const int32_t* orig_id;   /* [m] input arc index */
+} iso_ch_view;
+int  iso_ch_view_arrays(const iso_ch* ch, iso_ch_view* out);
+/* Position of original vertex v in sweep order (descending level), or -1. */
+int32_t iso_ch_sweep_position(const iso_ch* ch, int32_t v);
+void iso_free_ch(iso_ch* ch);
+
+/* ---------------------------------------------------------------------------
+ * Device graph.
+ * ------------------------------------------------------------------------- */
+
+/* Device memory comes from these callbacks (the Python binding backs them with
+ * PyTorch's caching allocator).  alloc returns NULL on failure; free accepts
+ * what alloc returned.  stream is the cudaStream_t the memory is used on. */
+typedef struct {
+    void* (*alloc)(void* ctx, size_t bytes, void* stream);
+    void  (*free)(void* ctx, void* ptr, void* stream);
+    void* ctx;
+} iso_alloc;
+
+/* Copy the CH to the current CUDA device (sweep-ordered CSRs, Section 2's
+ * "linear sweep over an edge array").  alloc may be NULL, in which case
+ * cudaMalloc/cudaFree are used.  The iso_ch may be freed
+ * afterwards.  Errors: ISO_E_INVAL, ISO_E_NOMEM, ISO_E_CUDA, ISO_E_NODEV. */
+int iso_upload_graph(const iso_ch* ch, const iso_alloc* alloc, void* stream, iso_graph** out);
+void iso_free_graph(iso_graph* g);
+
+/* ---------------------------------------------------------------------------
+ * Queries.
+ * ------------------------------------------------------------------------- */
+
+typedef struct {
+    int32_t threads_per_vertex; /* sweep threads per vertex (1,2,4,...,k/4 lanes each); 0 = auto */
+    int32_t ctas_per_sm;        /* persistent sweep CTAs per SM; 0 = auto (occupancy) */
+    int32_t fuse_width;         /* levels with fewer vertices run in one CTA between grid
+                                   barriers; 0 = auto, -1 = never fuse */
+    int32_t use_cuda_graph;     /* 1 = capture the launch sequence once per workspace and replay */
+    int64_t barrier_timeout_ns; /* give up a grid barrier after this long; 0 = 2 s */
+    int32_t debug_barrier_extra;/* testing only: the sweep's barriers wait for this many extra
+                                   arrivals that never come, so every wait times out */
+    int32_t reserved[7];        /* must be zero */
+} iso_query_opts;
+
+/* Answer k isochrone queries (source sources[i], limit taus[i]) in sweeps of
+ * up to 64 lanes.  sources/taus may be host or device memory (detected).
+ * On success out_offsets[0..k] (host or device) holds list boundaries and
+ * out_arcs[out_offsets[i] .. out_offsets[i+1]) the arc ids of query i in
+ * ascending order.  out_dist (nullable; host or device) receives the labels,
+ * query-major: out_dist[i*n + v] for original vertex v.  If the lists need
+ * more than cap entries, out_offsets is filled with the needed offsets, nothing
+ * is written to out_arcs, and ISO_E_OVERFLOW is returned.  Validation: k >= 0,
+ * 0 <= sources[i] < n, 0 <= taus[i] <= 0x7FFFFFFE - max_weight.
+ * The call returns after the results are in place (it synchronizes `stream`,
+ * the cudaStream_t to run on; NULL = the legacy default stream). */
+int iso_query(iso_graph* g, int32_t k, const int32_t* sources, const int32_t* taus,
+              int64_t* out_offsets, int32_t* out_arcs, int64_t cap, int32_t* out_dist,
+              const iso_query_opts* opts /* nullable */, void* stream);
+
+/* Workspaces hold the per-batch device buffers for up to `lanes` queries
+ * (lanes in 1..64) so that batches can be kept in flight on several streams. */
+int iso_workspace_create(iso_graph* g, int32_t lanes, const iso_query_opts* opts /* nullable */,
+                         void* stream, iso_workspace** out);
+/* Enqueue one batch of k <= lanes queries on `stream` and return without
+ * waiting for the device.  sources/taus: host or device memory (detected);
+ * host values are validated here, device values by the first kernel (a bad one
+ * makes iso_collect return ISO_E_INVAL).  flags: ISO_SUBMIT_DIST to also keep
+ * the labels for iso_collect's out_dist.  A workspace holds one batch at a
+ * time: collect before submitting again. */
+#define ISO_SUBMIT_DIST 1
+int iso_submit(iso_workspace* ws, int32_t k, const int32_t* sources, const int32_t* taus, int32_t flags,
+               void* stream);
+/* Wait for the batch last submitted on ws and copy its results as iso_query
+ * does (same layout, overflow and distance conventions). */
+int iso_collect(iso_workspace* ws, int64_t* out_offsets, int32_t* out_arcs, int64_t cap,
+                int32_t* out_dist);
+/* Per-phase device times of the last collected batch in milliseconds:
+ * [0] upward search, [1] sweep, [2] emission, [3] sort + gather. */
+int iso_workspace_timings(const iso_workspace* ws, float* ms4);
+void iso_free_workspace(iso_workspace* ws);
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char* iso_last_error(void);
+/* Library version string. */
+const char* iso_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ISO_H */

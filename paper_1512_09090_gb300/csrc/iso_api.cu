@@ -1,0 +1,639 @@
+// C ABI: device upload, workspaces, batched submission and result collection.
+//
+// A batch of up to K lanes runs as one fixed launch sequence on the caller's
+// stream (optionally captured once into a CUDA graph and replayed):
+//   memset control block -> k_upward (one CTA per lane) -> k_sweep (persistent,
+//   cooperative) -> k_emit -> k_sort_gather [-> k_dist] -> copy summary to host.
+// Collecting waits for the summary, grows internal buffers and replays the
+// batch if an upward search or an emission list outgrew them, then copies the
+// lists (and labels) to the caller.  No step falls back to the CPU: without a
+// device every call returns ISO_E_NODEV.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <vector>
+
+#include "ch_internal.h"
+#include "iso_device.cuh"
+#include "../../include/iso.h"
+
+namespace {
+
+using namespace isod;
+
+int cuda_status(cudaError_t e) {
+    return e == cudaErrorMemoryAllocation ? ISO_E_NOMEM
+         : (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) ? ISO_E_NODEV
+         : ISO_E_CUDA;
+}
+
+#define ISO_CK(call)                                                                          \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            iso::set_error("%s failed: %s", #call, cudaGetErrorString(e_));                   \
+            return cuda_status(e_);                                                           \
+        }                                                                                     \
+    } while (0)
+
+struct Allocator {
+    iso_alloc cb{};
+    bool custom = false;
+    void* get(size_t bytes, cudaStream_t s) {
+        if (bytes == 0) bytes = 16;
+        bytes = (bytes + 255) & ~(size_t)255;
+        if (custom) return cb.alloc(cb.ctx, bytes, s);
+        void* p = nullptr;
+        return cudaMalloc(&p, bytes) == cudaSuccess ? p : nullptr;
+    }
+    void put(void* p, cudaStream_t s) {
+        if (!p) return;
+        if (custom) cb.free(cb.ctx, p, s);
+        else cudaFree(p);
+    }
+};
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+constexpr int kMaxLanes = 64;
+
+int lanes_class(int k) {
+    if (k <= 1) return 1;
+    for (int K : {4, 8, 16, 32, 64})
+        if (k <= K) return K;
+    return 64;
+}
+
+int default_tpv(int K) { return K <= 8 ? 1 : K / 8; }
+
+}  // namespace
+
+struct iso_graph {
+    int device = 0;
+    int n = 0, L = 0, max_w = 0, tau_max = 0, num_sms = 0;
+    int64_t m = 0, m_down = 0, m_up = 0;
+    Allocator A;
+    cudaStream_t stream = nullptr;
+    uint32_t* down_off = nullptr;
+    int2* down_arc = nullptr;
+    uint32_t* up_off = nullptr;
+    int2* up_arc = nullptr;
+    uint32_t* orig_off = nullptr;
+    int32_t* orig_head = nullptr;
+    int32_t* orig_id = nullptr;
+    int32_t* perm = nullptr;
+    int32_t* pos = nullptr;
+    int32_t* level_off = nullptr;
+    std::vector<int32_t> h_level_off;
+    std::mutex mu;
+    iso_workspace* query_ws[7] = {};
+    std::vector<void*> owned;
+
+    template <class T>
+    int upload(T** dst, const T* src, size_t count) {
+        *dst = (T*)A.get(count * sizeof(T), stream);
+        if (!*dst) { iso::set_error("iso_upload_graph: device allocation of %zu bytes failed", count * sizeof(T)); return ISO_E_NOMEM; }
+        owned.push_back(*dst);
+        if (count) ISO_CK(cudaMemcpyAsync(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice, stream));
+        return ISO_OK;
+    }
+};
+
+struct iso_workspace {
+    iso_graph* g = nullptr;
+    int K = 0, tpv = 0, grid = 0, fuse_width = 0;
+    bool use_graph = false;
+    long long timeout_ns = 2000000000LL;
+    int bar_extra = 0;
+    cudaStream_t stream = nullptr;  // stream of the last submit
+    // device buffers
+    uint32_t* d = nullptr;
+    void* mask = nullptr;
+    uint8_t* upflag = nullptr;
+    int32_t* io = nullptr;       // src[K], tau[K]
+    int32_t* ctl = nullptr;      // status[4], bar[2], pad[2], ecnt[K], upcnt[K]
+    int2* pairs = nullptr;
+    uint32_t* gtab = nullptr;
+    int gcap = 1 << 14;
+    int32_t* ebuf = nullptr;
+    int32_t* tmp = nullptr;
+    int ecap = 1 << 15;
+    int32_t* out = nullptr;
+    int64_t* out_off = nullptr;
+    int4* sched = nullptr;
+    int nsched = 0;
+    int32_t* dist = nullptr;     // [K * n] labels, query-major, original vertex order
+    // pinned host mirrors
+    int32_t* h_io = nullptr;     // src[K], tau[K]
+    int32_t* h_ctl = nullptr;    // ctl after the last batch
+    // state of the last batch
+    int k = 0;
+    bool want_dist = false;
+    bool submitted = false;
+    float phase_ms[4] = {};
+    cudaEvent_t ev[6] = {};
+    cudaGraphExec_t gexec[2] = {};  // indexed by want_dist
+    bool graph_failed = false;
+    std::vector<void*> owned;
+
+    int32_t* src() { return io; }
+    int32_t* tau() { return io + K; }
+    int32_t* status() { return ctl; }
+    uint32_t* bar() { return (uint32_t*)(ctl + 4); }
+    int32_t* ecnt() { return ctl + 8; }
+    int32_t* upcnt() { return ctl + 8 + K; }
+    size_t ctl_words() const { return 8 + 2 * (size_t)K; }
+
+    void* alloc(size_t bytes) {
+        void* p = g->A.get(bytes, stream);
+        if (p) owned.push_back(p);
+        return p;
+    }
+    void release(void*& p) {
+        if (!p) return;
+        owned.erase(std::remove(owned.begin(), owned.end(), p), owned.end());
+        g->A.put(p, stream);
+        p = nullptr;
+    }
+    void drop_graphs() {
+        for (auto& x : gexec)
+            if (x) { cudaGraphExecDestroy(x); x = nullptr; }
+    }
+};
+
+namespace {
+
+int build_schedule(iso_workspace* ws) {
+    iso_graph* g = ws->g;
+    std::vector<int4> steps;
+    for (int j = 0; j < g->L;) {
+        const int w = g->h_level_off[j + 1] - g->h_level_off[j];
+        if (ws->fuse_width > 0 && w < ws->fuse_width) {
+            int j1 = j + 1;
+            while (j1 < g->L && g->h_level_off[j1 + 1] - g->h_level_off[j1] < ws->fuse_width) ++j1;
+            steps.push_back(make_int4(kStepFused, j, j1, 0));
+            j = j1;
+        } else {
+            steps.push_back(make_int4(kStepWide, j, j + 1, 0));
+            ++j;
+        }
+    }
+    ws->nsched = (int)steps.size();
+    ws->sched = (int4*)ws->alloc(steps.size() * sizeof(int4));
+    if (!ws->sched) { iso::set_error("workspace: device allocation failed"); return ISO_E_NOMEM; }
+    ISO_CK(cudaMemcpyAsync(ws->sched, steps.data(), steps.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                           ws->stream));
+    ISO_CK(cudaStreamSynchronize(ws->stream));
+    return ISO_OK;
+}
+
+int alloc_up(iso_workspace* ws) {
+    ws->pairs = (int2*)ws->alloc((size_t)ws->K * ws->gcap * sizeof(int2));
+    ws->gtab = (uint32_t*)ws->alloc((size_t)ws->K * 5 * ws->gcap * sizeof(uint32_t));
+    if (!ws->pairs || !ws->gtab) { iso::set_error("workspace: device allocation failed"); return ISO_E_NOMEM; }
+    return ISO_OK;
+}
+
+int alloc_emit(iso_workspace* ws) {
+    const size_t cells = (size_t)ws->K * ws->ecap;
+    ws->ebuf = (int32_t*)ws->alloc(cells * 4);
+    ws->tmp = (int32_t*)ws->alloc(cells * 4);
+    ws->out = (int32_t*)ws->alloc(cells * 4);
+    if (!ws->ebuf || !ws->tmp || !ws->out) { iso::set_error("workspace: device allocation failed"); return ISO_E_NOMEM; }
+    return ISO_OK;
+}
+
+// Timing events become event-record nodes when the sequence is captured.
+cudaError_t record(cudaEvent_t e, cudaStream_t s, bool capturing) {
+    return capturing ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaEventRecord(e, s);
+}
+
+// The launch sequence of one batch on ws->stream; inputs are already in ws->io.
+int enqueue(iso_workspace* ws, bool want_dist, bool capturing) {
+    iso_graph* g = ws->g;
+    cudaStream_t s = ws->stream;
+    const int K = ws->K;
+    ISO_CK(cudaMemsetAsync(ws->ctl, 0, ws->ctl_words() * 4, s));
+    ISO_CK(record(ws->ev[0], s, capturing));
+
+    UpParams up{};
+    up.up_off = g->up_off; up.up_arc = g->up_arc; up.pos = g->pos;
+    up.src = ws->src(); up.tau = ws->tau();
+    up.pairs = ws->pairs; up.cnt = ws->upcnt(); up.gtab = ws->gtab; up.status = ws->status();
+    up.n = g->n; up.cap = ws->gcap; up.gcap = ws->gcap; up.tau_max = g->tau_max;
+    ISO_CK(iso_launch_upward(up, K, s));
+    ISO_CK(record(ws->ev[1], s, capturing));
+
+    SweepParams sw{};
+    sw.down_off = g->down_off; sw.down_arc = g->down_arc; sw.level_off = g->level_off;
+    sw.sched = ws->sched; sw.pairs = ws->pairs; sw.cnt = ws->upcnt(); sw.tau = ws->tau();
+    sw.d = ws->d; sw.mask = ws->mask; sw.upflag = ws->upflag; sw.bar = ws->bar(); sw.status = ws->status();
+    sw.timeout_ns = ws->timeout_ns; sw.n = g->n; sw.L = g->L; sw.nsched = ws->nsched; sw.cap = ws->gcap;
+    sw.last_level_block = g->L - 1; sw.write_all = want_dist ? 1 : 0; sw.bar_extra = ws->bar_extra;
+    ISO_CK(iso_launch_sweep(sw, K, ws->tpv, ws->grid, s));
+    ISO_CK(record(ws->ev[2], s, capturing));
+
+    EmitParams em{};
+    em.orig_off = g->orig_off; em.orig_head = g->orig_head; em.orig_id = g->orig_id; em.mask = ws->mask;
+    em.ecnt = ws->ecnt(); em.ebuf = ws->ebuf; em.n = g->n; em.ecap = ws->ecap;
+    ISO_CK(iso_launch_emit(em, K, g->num_sms * 8, s));
+    ISO_CK(record(ws->ev[3], s, capturing));
+
+    GatherParams ga{};
+    ga.ebuf = ws->ebuf; ga.ecnt = ws->ecnt(); ga.tmp = ws->tmp; ga.out = ws->out; ga.out_off = ws->out_off;
+    ga.k = K; ga.ecap = ws->ecap;
+    ISO_CK(iso_launch_sort_gather(ga, K, s));
+    if (want_dist) {
+        DistParams dp{};
+        dp.d = ws->d; dp.perm = g->perm; dp.out = ws->dist; dp.n = g->n; dp.k = K; dp.K = K;
+        ISO_CK(iso_launch_dist(dp, s));
+    }
+    ISO_CK(record(ws->ev[4], s, capturing));
+    ISO_CK(cudaMemcpyAsync(ws->h_ctl, ws->ctl, ws->ctl_words() * 4, cudaMemcpyDeviceToHost, s));
+    ISO_CK(record(ws->ev[5], s, capturing));
+    return ISO_OK;
+}
+
+int launch_batch(iso_workspace* ws, bool want_dist) {
+    if (want_dist && !ws->dist) {
+        ws->dist = (int32_t*)ws->alloc((size_t)ws->K * ws->g->n * 4);
+        if (!ws->dist) { iso::set_error("workspace: device allocation failed"); return ISO_E_NOMEM; }
+    }
+    if (ws->use_graph && !ws->graph_failed) {
+        cudaGraphExec_t& ex = ws->gexec[want_dist ? 1 : 0];
+        if (!ex) {
+            cudaGraph_t graph = nullptr;
+            bool ok = cudaStreamBeginCapture(ws->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            int rc = ok ? enqueue(ws, want_dist, true) : ISO_E_CUDA;
+            cudaError_t ce = ok ? cudaStreamEndCapture(ws->stream, &graph) : cudaErrorUnknown;
+            ok = ok && rc == ISO_OK && ce == cudaSuccess && graph &&
+                 cudaGraphInstantiate(&ex, graph, 0) == cudaSuccess;
+            if (graph) cudaGraphDestroy(graph);
+            if (!ok) {
+                cudaGetLastError();
+                ex = nullptr;
+                ws->graph_failed = true;  // run the same sequence without a graph from now on
+            }
+        }
+        if (ex) {
+            ISO_CK(cudaGraphLaunch(ex, ws->stream));
+            return ISO_OK;
+        }
+    }
+    return enqueue(ws, want_dist, false);
+}
+
+int copy_out(void* dst, const void* src, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) return ISO_OK;
+    ISO_CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
+    return ISO_OK;
+}
+
+int check_opts(const iso_query_opts* o) {
+    if (!o) return ISO_OK;
+    for (int r : o->reserved)
+        if (r) { iso::set_error("iso_query_opts: reserved fields must be zero"); return ISO_E_INVAL; }
+    if (o->threads_per_vertex < 0 || o->ctas_per_sm < 0 || o->fuse_width < -1 || o->barrier_timeout_ns < 0 ||
+        o->debug_barrier_extra < 0) {
+        iso::set_error("iso_query_opts: negative field");
+        return ISO_E_INVAL;
+    }
+    return ISO_OK;
+}
+
+}  // namespace
+
+extern "C" int iso_upload_graph(const iso_ch* ch, const iso_alloc* alloc, void* stream, iso_graph** out) {
+    iso::clear_error();
+    if (!ch || !out) { iso::set_error("iso_upload_graph: NULL argument"); return ISO_E_INVAL; }
+    *out = nullptr;
+    if (alloc && (!alloc->alloc || !alloc->free)) { iso::set_error("iso_upload_graph: incomplete allocator"); return ISO_E_INVAL; }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        iso::set_error("iso_upload_graph: no CUDA device");
+        return ISO_E_NODEV;
+    }
+    std::unique_ptr<iso_graph> g(new iso_graph());
+    ISO_CK(cudaGetDevice(&g->device));
+    ISO_CK(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device));
+    if (alloc) { g->A.cb = *alloc; g->A.custom = true; }
+    g->stream = (cudaStream_t)stream;
+    g->n = ch->n; g->L = ch->L; g->m = ch->m; g->max_w = ch->max_w;
+    g->m_down = ch->down_off.back(); g->m_up = ch->up_off.back();
+    g->tau_max = 0x7FFFFFFE - ch->max_w;
+    g->h_level_off = ch->level_off;
+    const size_t n = (size_t)ch->n;
+    std::vector<uint32_t> off32(n + 1);
+    std::vector<int2> arcs;
+    int rc = ISO_OK;
+    auto free_all = [&]() { for (void* p : g->owned) g->A.put(p, g->stream); g->owned.clear(); };
+    for (size_t i = 0; i <= n; ++i) off32[i] = (uint32_t)ch->down_off[i];
+    arcs.resize(ch->down_src.size() + 2);  // two spare entries keep 16-byte loads in bounds
+    for (size_t i = 0; i < ch->down_src.size(); ++i) arcs[i] = make_int2(ch->down_src[i], ch->down_w[i]);
+    arcs[arcs.size() - 1] = arcs[arcs.size() - 2] = make_int2(0, 0);
+    if ((rc = g->upload(&g->down_off, off32.data(), n + 1)) || (rc = g->upload(&g->down_arc, arcs.data(), arcs.size()))) {
+        free_all(); return rc;
+    }
+    ISO_CK(cudaStreamSynchronize(g->stream));
+    for (size_t i = 0; i <= n; ++i) off32[i] = (uint32_t)ch->up_off[i];
+    arcs.assign(ch->up_dst.size() + 2, make_int2(0, 0));
+    for (size_t i = 0; i < ch->up_dst.size(); ++i) arcs[i] = make_int2(ch->up_dst[i], ch->up_w[i]);
+    if ((rc = g->upload(&g->up_off, off32.data(), n + 1)) || (rc = g->upload(&g->up_arc, arcs.data(), arcs.size()))) {
+        free_all(); return rc;
+    }
+    ISO_CK(cudaStreamSynchronize(g->stream));
+    for (size_t i = 0; i <= n; ++i) off32[i] = (uint32_t)ch->orig_off[i];
+    if ((rc = g->upload(&g->orig_off, off32.data(), n + 1)) ||
+        (rc = g->upload(&g->orig_head, ch->orig_head.data(), ch->orig_head.size())) ||
+        (rc = g->upload(&g->orig_id, ch->orig_id.data(), ch->orig_id.size())) ||
+        (rc = g->upload(&g->perm, ch->perm.data(), n)) || (rc = g->upload(&g->pos, ch->pos.data(), n)) ||
+        (rc = g->upload(&g->level_off, ch->level_off.data(), ch->level_off.size()))) {
+        free_all(); return rc;
+    }
+    cudaError_t e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) { free_all(); iso::set_error("iso_upload_graph: %s", cudaGetErrorString(e)); return cuda_status(e); }
+    *out = g.release();
+    return ISO_OK;
+}
+
+extern "C" void iso_free_workspace(iso_workspace* ws);
+
+extern "C" void iso_free_graph(iso_graph* g) {
+    if (!g) return;
+    cudaDeviceSynchronize();
+    for (auto*& ws : g->query_ws) { iso_free_workspace(ws); ws = nullptr; }
+    for (void* p : g->owned) g->A.put(p, g->stream);
+    delete g;
+}
+
+extern "C" int iso_workspace_create(iso_graph* g, int32_t lanes, const iso_query_opts* opts, void* stream,
+                                    iso_workspace** out) {
+    iso::clear_error();
+    if (!g || !out) { iso::set_error("iso_workspace_create: NULL argument"); return ISO_E_INVAL; }
+    *out = nullptr;
+    if (lanes < 1 || lanes > kMaxLanes) { iso::set_error("iso_workspace_create: lanes must be in 1..64"); return ISO_E_INVAL; }
+    int rc = check_opts(opts);
+    if (rc) return rc;
+    std::unique_ptr<iso_workspace> ws(new iso_workspace());
+    ws->g = g;
+    ws->stream = (cudaStream_t)stream;
+    ws->K = lanes_class(lanes);
+    ws->tpv = (opts && opts->threads_per_vertex) ? opts->threads_per_vertex : default_tpv(ws->K);
+    if (!iso_sweep_supported(ws->K, ws->tpv)) {
+        iso::set_error("iso_workspace_create: %d threads per vertex unsupported for %d lanes", ws->tpv, ws->K);
+        return ISO_E_INVAL;
+    }
+    int block = 0;
+    int occ = iso_sweep_occupancy(ws->K, ws->tpv, &block);
+    if (occ <= 0) { iso::set_error("iso_workspace_create: sweep kernel cannot be resident"); return ISO_E_CUDA; }
+    const int per_sm = (opts && opts->ctas_per_sm) ? std::min<int>(opts->ctas_per_sm, occ) : occ;
+    ws->grid = g->num_sms * per_sm;
+    const int vpb = block / ws->tpv;
+    ws->fuse_width = !opts || opts->fuse_width == 0 ? vpb : (opts->fuse_width < 0 ? 0 : opts->fuse_width);
+    ws->use_graph = opts ? opts->use_cuda_graph != 0 : false;
+    if (opts && opts->barrier_timeout_ns) ws->timeout_ns = opts->barrier_timeout_ns;
+    ws->bar_extra = opts ? opts->debug_barrier_extra : 0;
+    auto fail = [&](int code) {
+        for (void* p : ws->owned) g->A.put(p, ws->stream);
+        ws->owned.clear();
+        if (ws->h_io) cudaFreeHost(ws->h_io);
+        if (ws->h_ctl) cudaFreeHost(ws->h_ctl);
+        ws->h_io = ws->h_ctl = nullptr;
+        return code;
+    };
+    const size_t n = (size_t)g->n, K = (size_t)ws->K;
+    const size_t mask_bytes = K <= 8 ? 1 : K / 8;
+    ws->d = (uint32_t*)ws->alloc(n * K * 4);
+    ws->mask = ws->alloc(n * mask_bytes);
+    ws->upflag = (uint8_t*)ws->alloc(n);
+    ws->io = (int32_t*)ws->alloc(2 * K * 4);
+    ws->ctl = (int32_t*)ws->alloc(ws->ctl_words() * 4);
+    ws->out_off = (int64_t*)ws->alloc((K + 1) * 8);
+    if (!ws->d || !ws->mask || !ws->upflag || !ws->io || !ws->ctl || !ws->out_off) {
+        iso::set_error("iso_workspace_create: device allocation failed");
+        return fail(ISO_E_NOMEM);
+    }
+    if ((rc = alloc_up(ws.get())) || (rc = alloc_emit(ws.get())) || (rc = build_schedule(ws.get()))) return fail(rc);
+    if (cudaMallocHost(&ws->h_io, 2 * K * 4) != cudaSuccess ||
+        cudaMallocHost(&ws->h_ctl, ws->ctl_words() * 4) != cudaSuccess) {
+        cudaGetLastError();
+        iso::set_error("iso_workspace_create: pinned host allocation failed");
+        return fail(ISO_E_NOMEM);
+    }
+    for (auto& e : ws->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); iso::set_error("iso_workspace_create: event"); return fail(ISO_E_CUDA); }
+    if (cudaMemsetAsync(ws->upflag, 0, n, ws->stream) != cudaSuccess ||
+        cudaStreamSynchronize(ws->stream) != cudaSuccess) {
+        cudaGetLastError();
+        iso::set_error("iso_workspace_create: initialisation failed");
+        return fail(ISO_E_CUDA);
+    }
+    *out = ws.release();
+    return ISO_OK;
+}
+
+extern "C" void iso_free_workspace(iso_workspace* ws) {
+    if (!ws) return;
+    if (ws->stream) cudaStreamSynchronize(ws->stream);
+    ws->drop_graphs();
+    for (auto& e : ws->ev)
+        if (e) cudaEventDestroy(e);
+    for (void* p : ws->owned) ws->g->A.put(p, ws->stream);
+    if (ws->h_io) cudaFreeHost(ws->h_io);
+    if (ws->h_ctl) cudaFreeHost(ws->h_ctl);
+    delete ws;
+}
+
+namespace {
+int submit_impl(iso_workspace* ws, int32_t k, const int32_t* sources, const int32_t* taus, bool want_dist,
+                cudaStream_t stream) {
+    iso_graph* g = ws->g;
+    if (k < 0 || k > ws->K) { iso::set_error("iso_submit: k=%d outside 0..%d", k, ws->K); return ISO_E_INVAL; }
+    if (k > 0 && (!sources || !taus)) { iso::set_error("iso_submit: NULL sources or taus"); return ISO_E_INVAL; }
+    if (ws->stream != stream) { ws->drop_graphs(); ws->stream = stream; }
+    const bool dev_s = is_device_ptr(sources), dev_t = is_device_ptr(taus);
+    const int K = ws->K;
+    for (int i = 0; i < 2 * K; ++i) ws->h_io[i] = -1;
+    if (!dev_s || !dev_t) {
+        for (int i = 0; i < k; ++i) {
+            if (!dev_s) {
+                if (sources[i] < 0 || sources[i] >= g->n) {
+                    iso::set_error("iso_submit: source %d of query %d outside [0,%d)", sources[i], i, g->n);
+                    return ISO_E_INVAL;
+                }
+                ws->h_io[i] = sources[i];
+            }
+            if (!dev_t) {
+                if (taus[i] < 0 || taus[i] > g->tau_max) {
+                    iso::set_error("iso_submit: limit %d of query %d outside [0,%d]", taus[i], i, g->tau_max);
+                    return ISO_E_INVAL;
+                }
+                ws->h_io[K + i] = taus[i];
+            }
+        }
+    }
+    for (int i = k; i < K; ++i) ws->h_io[K + i] = 0;  // idle lanes: src -1, tau 0
+    ISO_CK(cudaMemcpyAsync(ws->io, ws->h_io, 2 * (size_t)K * 4, cudaMemcpyHostToDevice, stream));
+    if (dev_s && k) ISO_CK(cudaMemcpyAsync(ws->io, sources, (size_t)k * 4, cudaMemcpyDeviceToDevice, stream));
+    if (dev_t && k) ISO_CK(cudaMemcpyAsync(ws->io + K, taus, (size_t)k * 4, cudaMemcpyDeviceToDevice, stream));
+    ws->k = k;
+    ws->want_dist = want_dist;
+    int rc = launch_batch(ws, want_dist);
+    if (rc) return rc;
+    ws->submitted = true;
+    return ISO_OK;
+}
+
+int collect_impl(iso_workspace* ws, int64_t* out_offsets, int32_t* out_arcs, int64_t cap, int32_t* out_dist) {
+    if (!ws->submitted) { iso::set_error("iso_collect: nothing submitted"); return ISO_E_INVAL; }
+    if (!out_offsets) { iso::set_error("iso_collect: out_offsets is NULL"); return ISO_E_INVAL; }
+    if (out_dist && !ws->want_dist) { iso::set_error("iso_collect: distances were not requested at submit"); return ISO_E_INVAL; }
+    for (int attempt = 0;; ++attempt) {
+        ISO_CK(cudaEventSynchronize(ws->ev[5]));
+        const int st = ws->h_ctl[0];
+        if (st == kStTimeout) { ws->submitted = false; iso::set_error("sweep: a grid barrier timed out"); return ISO_E_TIMEOUT; }
+        if (st == kStBadInput) { ws->submitted = false; iso::set_error("query: a source or limit failed validation"); return ISO_E_INVAL; }
+        int grow_up = st == kStUpOverflow;
+        int need = 0;
+        for (int i = 0; i < ws->K; ++i) need = std::max(need, ws->h_ctl[8 + i]);
+        const bool grow_emit = need > ws->ecap;
+        if (!grow_up && !grow_emit) break;
+        if (attempt > 8) { iso::set_error("collect: buffers kept overflowing"); return ISO_E_NOMEM; }
+        ws->drop_graphs();
+        if (grow_up) {
+            ws->release(*(void**)&ws->pairs);
+            ws->release(*(void**)&ws->gtab);
+            ws->gcap *= 4;
+            if (int rc = alloc_up(ws)) return rc;
+        }
+        if (grow_emit) {
+            ws->release(*(void**)&ws->ebuf);
+            ws->release(*(void**)&ws->tmp);
+            ws->release(*(void**)&ws->out);
+            while (ws->ecap < need) ws->ecap *= 2;
+            if (int rc = alloc_emit(ws)) return rc;
+        }
+        if (int rc = launch_batch(ws, ws->want_dist)) return rc;
+    }
+    float t[4] = {};
+    for (int i = 0; i < 4; ++i) cudaEventElapsedTime(&t[i], ws->ev[i], ws->ev[i + 1]);
+    for (int i = 0; i < 4; ++i) ws->phase_ms[i] = t[i];
+    std::vector<int64_t> off(ws->k + 1, 0);
+    for (int i = 0; i < ws->k; ++i) off[i + 1] = off[i] + ws->h_ctl[8 + i];
+    const int64_t total = off[ws->k];
+    cudaStream_t s = ws->stream;
+    if (int rc = copy_out(out_offsets, off.data(), off.size() * 8, s)) return rc;
+    int rc = ISO_OK;
+    if (total > cap) {
+        iso::set_error("iso_collect: %lld arcs do not fit capacity %lld", (long long)total, (long long)cap);
+        rc = ISO_E_OVERFLOW;
+    } else if (total > 0) {
+        if (!out_arcs) { iso::set_error("iso_collect: out_arcs is NULL"); return ISO_E_INVAL; }
+        if (int r2 = copy_out(out_arcs, ws->out, (size_t)total * 4, s)) return r2;
+    }
+    if (out_dist && rc == ISO_OK)
+        if (int r2 = copy_out(out_dist, ws->dist, (size_t)ws->k * ws->g->n * 4, s)) return r2;
+    ISO_CK(cudaStreamSynchronize(s));
+    return rc;
+}
+}  // namespace
+
+extern "C" int iso_submit(iso_workspace* ws, int32_t k, const int32_t* sources, const int32_t* taus, int32_t flags,
+                          void* stream) {
+    iso::clear_error();
+    if (!ws) { iso::set_error("iso_submit: NULL workspace"); return ISO_E_INVAL; }
+    if (flags & ~ISO_SUBMIT_DIST) { iso::set_error("iso_submit: unknown flags"); return ISO_E_INVAL; }
+    return submit_impl(ws, k, sources, taus, (flags & ISO_SUBMIT_DIST) != 0, (cudaStream_t)stream);
+}
+
+extern "C" int iso_collect(iso_workspace* ws, int64_t* out_offsets, int32_t* out_arcs, int64_t cap,
+                           int32_t* out_dist) {
+    iso::clear_error();
+    if (!ws) { iso::set_error("iso_collect: NULL workspace"); return ISO_E_INVAL; }
+    return collect_impl(ws, out_offsets, out_arcs, cap, out_dist);
+}
+
+extern "C" int iso_workspace_timings(const iso_workspace* ws, float* ms4) {
+    if (!ws || !ms4) return ISO_E_INVAL;
+    std::memcpy(ms4, ws->phase_ms, sizeof(ws->phase_ms));
+    return ISO_OK;
+}
+
+namespace {
+// Does workspace ws run with the settings that options o ask for?
+bool same_config(const iso_workspace* ws, const iso_query_opts& o) {
+    const int tpv = o.threads_per_vertex ? o.threads_per_vertex : default_tpv(ws->K);
+    int block = 0;
+    const int occ = iso_sweep_occupancy(ws->K, tpv, &block);
+    const int per_sm = o.ctas_per_sm ? std::min<int>(o.ctas_per_sm, occ) : occ;
+    const int fuse = o.fuse_width == 0 ? block / std::max(tpv, 1) : (o.fuse_width < 0 ? 0 : o.fuse_width);
+    const long long timeout = o.barrier_timeout_ns ? o.barrier_timeout_ns : 2000000000LL;
+    return ws->tpv == tpv && ws->grid == ws->g->num_sms * per_sm && ws->fuse_width == fuse &&
+           ws->use_graph == (o.use_cuda_graph != 0) && ws->timeout_ns == timeout &&
+           ws->bar_extra == o.debug_barrier_extra;
+}
+}  // namespace
+
+extern "C" int iso_query(iso_graph* g, int32_t k, const int32_t* sources, const int32_t* taus, int64_t* out_offsets,
+                         int32_t* out_arcs, int64_t cap, int32_t* out_dist, const iso_query_opts* opts,
+                         void* stream) {
+    iso::clear_error();
+    if (!g || !out_offsets) { iso::set_error("iso_query: NULL argument"); return ISO_E_INVAL; }
+    if (k < 0) { iso::set_error("iso_query: k < 0"); return ISO_E_INVAL; }
+    if (k > 0 && (!sources || !taus)) { iso::set_error("iso_query: NULL sources or taus"); return ISO_E_INVAL; }
+    if (int rc = check_opts(opts)) return rc;
+    std::lock_guard<std::mutex> lock(g->mu);
+    const bool dev_off = is_device_ptr(out_offsets);
+    const bool dev_src = is_device_ptr(sources), dev_tau = is_device_ptr(taus);
+    std::vector<int64_t> offs((size_t)k + 1, 0);
+    int64_t used = 0;
+    int result = ISO_OK;
+    const int chunk = kMaxLanes;
+    for (int b = 0; b < k || (k == 0 && b == 0); b += chunk) {
+        const int kb = std::min(chunk, k - b);
+        if (kb <= 0) break;
+        const int K = lanes_class(kb);
+        int ci = 0;
+        while ((1 << ci) < K) ++ci;
+        iso_workspace*& ws = g->query_ws[ci];
+        iso_query_opts o = opts ? *opts : iso_query_opts{};
+        if (!opts) o.use_cuda_graph = 1;
+        if (ws && !same_config(ws, o)) {
+            iso_free_workspace(ws);
+            ws = nullptr;
+        }
+        if (!ws) {
+            if (int rc = iso_workspace_create(g, K, &o, stream, &ws)) return rc;
+        }
+        if (int rc = submit_impl(ws, kb, dev_src ? sources + b : sources + b, dev_tau ? taus + b : taus + b,
+                                 out_dist != nullptr, (cudaStream_t)stream))
+            return rc;
+        std::vector<int64_t> lo(kb + 1);
+        const int64_t room = result == ISO_OK ? std::max<int64_t>(0, cap - used) : 0;
+        int32_t* dst = out_arcs ? out_arcs + used : nullptr;
+        int32_t* ddst = out_dist ? out_dist + (size_t)b * g->n : nullptr;
+        int rc = collect_impl(ws, lo.data(), dst, room, ddst);
+        if (rc == ISO_E_OVERFLOW) result = ISO_E_OVERFLOW;
+        else if (rc) return rc;
+        for (int i = 0; i < kb; ++i) offs[b + i + 1] = used + lo[i + 1];
+        used += lo[kb];
+    }
+    if (dev_off) ISO_CK(cudaMemcpyAsync(out_offsets, offs.data(), offs.size() * 8, cudaMemcpyHostToDevice, (cudaStream_t)stream));
+    else std::memcpy(out_offsets, offs.data(), offs.size() * 8);
+    ISO_CK(cudaStreamSynchronize((cudaStream_t)stream));
+    if (result == ISO_E_OVERFLOW)
+        iso::set_error("iso_query: %lld arcs do not fit capacity %lld", (long long)used, (long long)cap);
+    return result;
+}

@@ -1,0 +1,109 @@
+// Device-side types shared by the isochrone kernels and their launchers.
+//
+// Layouts (all in HBM, sweep order = descending CH level):
+//   d[v*K + i]      uint32 label of vertex v for lane i (query i of the batch);
+//                   0x7FFFFFFF = out of range.  K lanes per row, K in {1,4,...,64}.
+//   mask[v]         K-bit word, bit i set iff v is in range for lane i.
+//   upflag[v]       1 while d[v*K..] holds upward-search labels not yet consumed
+//                   by the sweep (the sweep clears it).
+//   down arcs       int2 {src, len} grouped by head, heads in sweep order.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace isod {
+
+constexpr uint32_t kInf = 0x7FFFFFFFu;
+
+// Device status word values (status[0]); the host maps them to ISO_E_*.
+enum : int {
+    kStOk = 0,
+    kStTimeout = 1,      // a grid barrier gave up
+    kStBadInput = 2,     // a source or limit failed validation on the device
+    kStUpOverflow = 3,   // upward search space exceeded the global table
+};
+
+// Sweep schedule step: x = kind (0 wide level, 1 run of narrow levels done by
+// CTA 0), y = first level block, z = one past the last level block.
+enum : int { kStepWide = 0, kStepFused = 1 };
+
+struct UpParams {
+    const uint32_t* up_off;   // [n+1]
+    const int2* up_arc;       // {dst, len}, dst a sweep position
+    const int32_t* pos;       // original id -> sweep position
+    const int32_t* src;       // [K] original ids, -1 = idle lane
+    const int32_t* tau;       // [K]
+    int2* pairs;              // [K * cap] {vertex, label} per lane
+    int32_t* cnt;             // [K]
+    uint32_t* gtab;           // [K * 3 * gcap] global fallback tables
+    int32_t* status;
+    int n;
+    int cap;                  // entries per lane in pairs (== gcap)
+    int gcap;                 // power of two
+    int tau_max;
+};
+
+struct SweepParams {
+    const uint32_t* down_off;  // [n+1]
+    const int2* down_arc;      // {src, len}
+    const int32_t* level_off;  // [L+1]
+    const int4* sched;         // [nsched]
+    const int2* pairs;         // upward labels, [K * cap]
+    const int32_t* cnt;        // [K]
+    const int32_t* tau;        // [K]
+    uint32_t* d;               // [n*K]
+    void* mask;                // [n] K-bit words
+    uint8_t* upflag;           // [n]
+    uint32_t* bar;             // [2] arrival count, generation
+    int32_t* status;
+    long long timeout_ns;
+    int n, L, nsched, cap;
+    int last_level_block;      // index j of the lowest level (its d rows need no store)
+    int write_all;             // store every d row (distances requested)
+    int bar_extra;             // testing: extra arrivals a barrier waits for
+};
+
+struct EmitParams {
+    const uint32_t* orig_off;  // [n+1]
+    const int32_t* orig_head;  // sweep positions
+    const int32_t* orig_id;
+    const void* mask;
+    int32_t* ecnt;             // [K]
+    int32_t* ebuf;             // [K * ecap]
+    int n, ecap;
+};
+
+struct GatherParams {
+    int32_t* ebuf;             // sorted per-lane segments [K * ecap]
+    const int32_t* ecnt;       // [K]
+    int32_t* tmp;              // [K * ecap] scratch for large sorts
+    int32_t* out;              // contiguous lists
+    int64_t* out_off;          // [K+1]
+    int k, ecap;
+    int key_bits;              // bits needed for arc ids
+};
+
+struct DistParams {
+    const uint32_t* d;
+    const int32_t* perm;
+    int32_t* out;              // [k * n], query-major, original vertex order
+    int n, k, K;
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+}  // namespace isod
+
+// Launchers (one translation unit each); return the launch's cudaError_t.
+cudaError_t iso_launch_upward(const isod::UpParams& p, int K, cudaStream_t s);
+cudaError_t iso_launch_sweep(const isod::SweepParams& p, int K, int tpv, int grid, cudaStream_t s);
+int iso_sweep_occupancy(int K, int tpv, int* block);
+bool iso_sweep_supported(int K, int tpv);
+cudaError_t iso_launch_emit(const isod::EmitParams& p, int K, int grid, cudaStream_t s);
+cudaError_t iso_launch_sort_gather(const isod::GatherParams& p, int K, cudaStream_t s);
+cudaError_t iso_launch_dist(const isod::DistParams& p, cudaStream_t s);

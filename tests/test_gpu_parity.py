@@ -1,0 +1,182 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Distances (clamped to INF beyond tau) and sorted isochrone-edge lists must be
+bit-exact: lengths and labels are int32 and no approximate arithmetic is
+involved.  Covers every lane class (k = 1..64), every threads-per-vertex
+variant, level fusion on and off, CUDA graphs on and off, host and device
+buffers, uneven limits, duplicate sources, degenerate graphs, overflow,
+argument errors and the barrier timeout."""
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1512_09090_gb300 as P
+from paper_1512_09090_gb300 import synth
+
+from helpers import INF, arcs_of, workload
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+_DEV = {}
+
+
+def dev_graph(name):
+    if name not in _DEV:
+        g, ch = workload(name)
+        _DEV[name] = (g, P.iso_upload_graph(ch))
+    return _DEV[name]
+
+
+def check_batch(g, dg, srcs, taus, want_dist=True, **opts):
+    off, arcs, dist = P.iso_query(dg, srcs, taus, want_dist=want_dist, **opts)
+    o_off, o_arcs, o_dist = oracle.query_batch(g.n, g.tail, g.head, g.weight, srcs, taus, want_dist=want_dist,
+                                               threads=8)
+    assert np.array_equal(off, o_off)
+    assert np.array_equal(arcs, o_arcs)
+    if want_dist:
+        assert np.array_equal(dist, o_dist)
+    return off, arcs
+
+
+def test_golden_hand_cases(golden_cases):
+    for case in golden_cases:
+        n, t, h, w = arcs_of(case)
+        ch = P.iso_build_ch(n, t, h, w)
+        dg = P.iso_upload_graph(ch)
+        srcs = np.array([q["s"] for q in case["queries"]], np.int32)
+        taus = np.array([q["tau"] for q in case["queries"]], np.int32)
+        off, arcs, dist = P.iso_query(dg, srcs, taus, want_dist=True)
+        for i, q in enumerate(case["queries"]):
+            assert arcs[off[i]:off[i + 1]].tolist() == q["expected"], (case["name"], q)
+            if "dist" in q:
+                want = [x if x <= q["tau"] else INF for x in q["dist"]]
+                assert dist[i].tolist() == want, (case["name"], q)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_small_graphs(seed):
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(1, 60))
+    g = synth.random_graph(n, int(rng.integers(0, 5 * n)), wmin=0, wmax=40, seed=seed)
+    dg = P.iso_upload_graph(P.iso_build_ch(g.n, g.tail, g.head, g.weight))
+    k = int(rng.integers(1, 65))
+    srcs = rng.integers(0, n, size=k).astype(np.int32)
+    taus = rng.integers(0, 200, size=k).astype(np.int32)
+    check_batch(g, dg, srcs, taus)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 8, 16, 17, 32, 64, 65, 130])
+def test_grid64_lane_counts(k):
+    g, dg = dev_graph("grid64")
+    srcs = synth.draw_sources(g, k, 1000 + k)
+    taus = synth.draw_taus_uniform(k, 0, 4000, 2000 + k)
+    check_batch(g, dg, srcs, taus)
+
+
+@pytest.mark.parametrize("k,tpv", [(8, 2), (16, 1), (16, 2), (16, 4), (32, 1), (32, 2), (32, 4), (32, 8),
+                                   (64, 1), (64, 2), (64, 4), (64, 8), (64, 16)])
+def test_threads_per_vertex_variants(k, tpv):
+    g, dg = dev_graph("grid64")
+    srcs = synth.draw_sources(g, k, 7)
+    taus = synth.draw_taus_uniform(k, 300, 3000, 8)
+    check_batch(g, dg, srcs, taus, threads_per_vertex=tpv)
+
+
+@pytest.mark.parametrize("fuse", [-1, 1, 64, 100000])
+@pytest.mark.parametrize("graph", [0, 1])
+def test_fusion_and_cuda_graph(fuse, graph):
+    g, dg = dev_graph("grid64")
+    srcs = synth.draw_sources(g, 16, 5)
+    taus = synth.draw_taus_uniform(16, 0, 3000, 6)
+    check_batch(g, dg, srcs, taus, fuse_width=fuse, use_cuda_graph=graph)
+
+
+def test_duplicate_sources_and_extreme_limits():
+    g, dg = dev_graph("grid64")
+    s = synth.draw_sources(g, 1, 3)[0]
+    tmax = 0x7FFFFFFE - int(g.weight.max())
+    srcs = np.array([s, s, s, s, s, 0, 0, 17], np.int32)
+    taus = np.array([0, 1500, 1500, 10 ** 6, tmax, 0, tmax, 1], np.int32)
+    check_batch(g, dg, srcs, taus)
+
+
+def test_grid1k_single_and_batched():
+    g, dg = dev_graph("grid1k")
+    srcs = synth.draw_sources(g, 6, 77)
+    for tau in (2000, 10000, 50000):
+        for s in srcs[:3]:
+            check_batch(g, dg, np.array([s], np.int32), np.array([tau], np.int32), want_dist=False)
+    taus = synth.draw_taus_uniform(16, 2000, 50000, 78)
+    check_batch(g, dg, synth.draw_sources(g, 16, 79), taus, want_dist=True)
+
+
+def test_device_buffers_and_workspaces():
+    g, dg = dev_graph("grid64")
+    k = 16
+    srcs = synth.draw_sources(g, k, 41)
+    taus = synth.draw_taus_uniform(k, 100, 3000, 42)
+    want_off, want_arcs, _ = oracle.query_batch(g.n, g.tail, g.head, g.weight, srcs, taus)
+    ds = torch.from_numpy(srcs).cuda()
+    dt = torch.from_numpy(taus).cuda()
+    o_off = torch.zeros(k + 1, dtype=torch.int64, device="cuda")
+    o_arcs = torch.zeros(int(want_off[-1]) + 5, dtype=torch.int32, device="cuda")
+    P.iso_query(dg, ds, dt, out_offsets=o_off, out_arcs=o_arcs)
+    assert np.array_equal(o_off.cpu().numpy(), want_off)
+    assert np.array_equal(o_arcs.cpu().numpy()[:want_off[-1]], want_arcs)
+    # two workspaces on two streams, interleaved
+    w1 = P.Workspace(dg, 16)
+    w2 = P.Workspace(dg, 64, use_cuda_graph=1)
+    srcs2 = synth.draw_sources(g, 40, 43)
+    taus2 = synth.draw_taus_uniform(40, 0, 5000, 44)
+    w1.submit(ds, dt)
+    w2.submit(srcs2, taus2)
+    off1, arcs1, _ = w1.collect()
+    off2, arcs2, _ = w2.collect()
+    assert np.array_equal(off1, want_off) and np.array_equal(arcs1, want_arcs)
+    e_off, e_arcs, _ = oracle.query_batch(g.n, g.tail, g.head, g.weight, srcs2, taus2)
+    assert np.array_equal(off2, e_off) and np.array_equal(arcs2, e_arcs)
+    t = w2.timings()
+    assert t["sweep"] > 0
+
+
+def test_overflow_reports_needed_offsets():
+    g, dg = dev_graph("grid64")
+    srcs = synth.draw_sources(g, 4, 1)
+    taus = np.full(4, 1500, np.int32)
+    want_off, _, _ = oracle.query_batch(g.n, g.tail, g.head, g.weight, srcs, taus)
+    off = np.zeros(5, np.int64)
+    small = np.zeros(3, np.int32)
+    with pytest.raises(P.IsoError) as e:
+        P.iso_query(dg, srcs, taus, out_offsets=off, out_arcs=small, cap=3)
+    assert e.value.code == P.ISO_E_OVERFLOW
+    assert np.array_equal(off, want_off)
+
+
+def test_argument_errors_and_recovery():
+    g, dg = dev_graph("grid64")
+    for s, t in [(-1, 10), (g.n, 10), (0, -1), (0, 0x7FFFFFFF)]:
+        with pytest.raises(P.IsoError) as e:
+            P.iso_query(dg, np.array([s], np.int32), np.array([t], np.int32))
+        assert e.value.code == P.ISO_E_INVAL
+    # invalid values in device memory are caught by the first kernel
+    with pytest.raises(P.IsoError) as e:
+        P.iso_query(dg, torch.tensor([g.n + 5], dtype=torch.int32, device="cuda"),
+                    torch.tensor([10], dtype=torch.int32, device="cuda"))
+    assert e.value.code == P.ISO_E_INVAL
+    check_batch(g, dg, synth.draw_sources(g, 4, 9), np.full(4, 900, np.int32))
+
+
+def test_barrier_timeout_is_reported_and_context_survives():
+    g, dg = dev_graph("grid64")
+    srcs = synth.draw_sources(g, 4, 2)
+    taus = np.full(4, 1000, np.int32)
+    with pytest.raises(P.IsoError) as e:
+        P.iso_query(dg, srcs, taus, debug_barrier_extra=1, barrier_timeout_ns=20_000_000)
+    assert e.value.code == P.ISO_E_TIMEOUT
+    torch.cuda.synchronize()
+    check_batch(g, dg, srcs, taus)
