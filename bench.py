@@ -36,6 +36,8 @@ WORKLOADS = {
     "grid18m_k16": dict(graph="grid18m", k=16, tau=("fixed", 36000)),
     # 18M-vertex graph, one source per launch
     "grid18m_k1": dict(graph="grid18m", k=1, tau=("uniform", 3600, 72000)),
+    "grid4m_k64": dict(graph="grid4m", k=64, tau=("uniform", 3600, 72000)),
+    "grid4m_k16": dict(graph="grid4m", k=16, tau=("fixed", 36000)),
     "grid1k_k1": dict(graph="grid1k", k=1, tau=("choice", (2000, 10000, 50000))),
     "grid1k_k16": dict(graph="grid1k", k=16, tau=("choice", (2000, 10000, 50000))),
     "grid1k_k64": dict(graph="grid1k", k=64, tau=("uniform", 2000, 50000)),
@@ -287,14 +289,16 @@ def main():
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    sweep_ms, lat_ms = [], []
+    sweep_ms, lat_ms, phases = [], [], []
     with ClockSampler(torch.cuda.current_device()) as clk:
         ev0.record(ws.stream)
         for i in range(args.steps):
             t0 = time.perf_counter()
             step(i)
             lat_ms.append((time.perf_counter() - t0) * 1e3)
-            sweep_ms.append(ws.timings()["sweep"])
+            ph = ws.timings()
+            phases.append(ph)
+            sweep_ms.append(ph["sweep"])
         ev1.record(ws.stream)
         torch.cuda.synchronize()
     el_ms = ev0.elapsed_time(ev1)
@@ -357,6 +361,7 @@ def main():
             "roofline": roof,
             "latency_ms": {"p50": round(lat[len(lat) // 2], 3), "p99": round(lat[min(len(lat) - 1,
                                                                                      int(0.99 * len(lat)))], 3)},
+            "phases_ms": {key: round(statistics.mean(p[key] for p in phases), 4) for key in phases[0]},
             "gpu_launches": 4 * args.steps, "e2e": e2e}
     clocks = clk.summary()
     if clocks:

@@ -141,6 +141,8 @@ WORKLOADS = {
     "grid64": dict(rows=64, cols=64, highways=(), seed=1),
     "grid1k": dict(rows=1000, cols=1000, highways=((32, 4),), seed=2),
     "grid18m": dict(rows=4243, cols=4243, highways=((16, 2), (128, 4), (1024, 8)), seed=3),
+    # a 4M-vertex graph with the same tiers, for profiling runs that must stay a few GB
+    "grid4m": dict(rows=2000, cols=2000, highways=((16, 2), (128, 4), (1024, 8)), seed=4),
 }
 
 
