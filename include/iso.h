@@ -184,6 +184,34 @@ int iso_collect(iso_workspace* ws, int64_t* out_offsets, int32_t* out_arcs, int6
 int iso_workspace_timings(const iso_workspace* ws, float* ms4);
 void iso_free_workspace(iso_workspace* ws);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free query (the paper has no counterpart; this is a library
+ * service).  For callers that cannot allocate device memory while answering a
+ * query -- a process whose device memory is fully reserved by another
+ * framework's pool, a latency-critical thread that must not wait on allocator
+ * locks or on the device-wide synchronisation a cudaFree can imply, a host that
+ * forbids allocation after start-up.  It runs the same kernels as iso_query on
+ * slices of one fixed static device array of ISO_NOALLOC_SCRATCH_BYTES bytes,
+ * which every GPU that loads the library holds until the process exits, and
+ * calls no allocator (CUDA's, PyTorch's or any other).
+ *
+ * Limits (larger requests return ISO_E_INVAL with a message): k <=
+ * ISO_NOALLOC_MAX_QUERIES, a graph of at most ISO_NOALLOC_MAX_VERTICES vertices
+ * and 4096 CH levels, at most ISO_NOALLOC_MAX_ARCS isochrone edges and 8192
+ * upward-search vertices per query.  Inputs, outputs, overflow and errors are
+ * as for iso_query (without out_dist).  The first call on each device looks up
+ * the array's device address, so make it before any stream capture on that
+ * device.  All calls share the array: calls that overlap on the GPU (two
+ * streams or two host threads at once) race and must be serialised by the
+ * caller.  The call synchronizes `stream` before returning.
+ * ------------------------------------------------------------------------- */
+#define ISO_NOALLOC_MAX_VERTICES (1 << 20)
+#define ISO_NOALLOC_MAX_QUERIES 4
+#define ISO_NOALLOC_MAX_ARCS 65536
+#define ISO_NOALLOC_SCRATCH_BYTES 23921408
+int iso_query_noalloc(iso_graph* g, int32_t k, const int32_t* sources, const int32_t* taus,
+                      int64_t* out_offsets, int32_t* out_arcs, int64_t cap, void* stream);
+
 /* Message describing the last error on the calling thread ("" if none). */
 const char* iso_last_error(void);
 /* Library version string. */

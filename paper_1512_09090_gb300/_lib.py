@@ -86,6 +86,7 @@ EXPORTS = {
     "iso_collect": (I32, [VP, VP, VP, I64, VP]),
     "iso_workspace_timings": (I32, [VP, VP]),
     "iso_free_workspace": (None, [VP]),
+    "iso_query_noalloc": (I32, [VP, I32, VP, VP, VP, VP, I64, VP]),
     "iso_last_error": (ctypes.c_char_p, []),
     "iso_version": (ctypes.c_char_p, []),
 }
@@ -363,3 +364,19 @@ class Workspace:
             self.free()
         except Exception:
             pass
+
+
+def iso_query_noalloc(g: DeviceGraph, sources, taus, out_offsets, out_arcs, cap: int | None = None, stream=None):
+    """Allocation-free query (iso_query_noalloc): the caller provides every output
+    buffer; the library uses only its fixed static device scratch array."""
+    k = int(len(sources))
+    if isinstance(sources, np.ndarray) or not hasattr(sources, "data_ptr"):
+        sources = np.ascontiguousarray(sources, dtype=np.int32)
+    if isinstance(taus, np.ndarray) or not hasattr(taus, "data_ptr"):
+        taus = np.ascontiguousarray(taus, dtype=np.int32)
+    if cap is None:
+        cap = int(out_arcs.numel() if hasattr(out_arcs, "numel") else out_arcs.size)
+    st = _stream_handle(stream if stream is not None else g.stream)
+    _check(lib().iso_query_noalloc(g.handle, k, _ptr(sources), _ptr(taus), _ptr(out_offsets), _ptr(out_arcs),
+                                   cap, st))
+    return out_offsets, out_arcs

@@ -637,3 +637,22 @@ extern "C" int iso_query(iso_graph* g, int32_t k, const int32_t* sources, const 
         iso::set_error("iso_query: %lld arcs do not fit capacity %lld", (long long)used, (long long)cap);
     return result;
 }
+
+// Read-only view of a device graph for the allocation-free entry point.
+struct iso_graph_view {
+    int n, L, tau_max, num_sms;
+    const uint32_t *down_off, *up_off, *orig_off;
+    const int2 *down_arc, *up_arc;
+    const int32_t *orig_head, *orig_id, *pos, *level_off;
+    const int32_t* h_level_off;
+};
+
+int iso_graph_view_of(const iso_graph* g, iso_graph_view* v) {
+    if (!g || !v) return ISO_E_INVAL;
+    v->n = g->n; v->L = g->L; v->tau_max = g->tau_max; v->num_sms = g->num_sms;
+    v->down_off = g->down_off; v->up_off = g->up_off; v->orig_off = g->orig_off;
+    v->down_arc = g->down_arc; v->up_arc = g->up_arc;
+    v->orig_head = g->orig_head; v->orig_id = g->orig_id; v->pos = g->pos; v->level_off = g->level_off;
+    v->h_level_off = g->h_level_off.data();
+    return ISO_OK;
+}
