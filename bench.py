@@ -234,6 +234,8 @@ def main():
     ap.add_argument("--tpv", type=int, default=0)
     ap.add_argument("--fuse", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--sweep-kernel", type=int, default=0)
+    ap.add_argument("--trace", action="store_true", help="print per-step sweep times to stderr")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -266,6 +268,10 @@ def main():
         opts["fuse_width"] = args.fuse
     if args.ctas_per_sm:
         opts["ctas_per_sm"] = args.ctas_per_sm
+    if args.sweep_kernel:
+        opts["sweep_kernel"] = args.sweep_kernel
+    if args.trace:
+        opts["record_trace"] = 1
     ws = P.Workspace(dg, k, **opts)
     nb = 16
     batches = []
@@ -302,6 +308,18 @@ def main():
         ev1.record(ws.stream)
         torch.cuda.synchronize()
     el_ms = ev0.elapsed_time(ev1)
+    if args.trace:
+        steps, ns = ws.trace()
+        lo = A["level_off"]
+        prev = 0
+        log("[trace] kind levels vertices us")
+        for st, t in zip(steps, ns):
+            if st[0] == 2:
+                log(f"[trace] prologue {t / 1e3:.1f}")
+                continue
+            nv = int(lo[st[2]] - lo[st[1]])
+            log(f"[trace] {st[0]} {st[1]}-{st[2]} {nv} {(t - prev) / 1e3:.1f}")
+            prev = max(prev, t)
     if dist:
         tt = torch.tensor([el_ms], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)

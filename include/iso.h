@@ -136,15 +136,18 @@ void iso_free_graph(iso_graph* g);
  * ------------------------------------------------------------------------- */
 
 typedef struct {
-    int32_t threads_per_vertex; /* sweep threads per vertex (1,2,4,...,k/4 lanes each); 0 = auto */
+    int32_t threads_per_vertex; /* sweep threads per vertex (each owns K/threads lanes); 0 = auto */
     int32_t ctas_per_sm;        /* persistent sweep CTAs per SM; 0 = auto (occupancy) */
-    int32_t fuse_width;         /* levels with fewer vertices run in one CTA between grid
-                                   barriers; 0 = auto, -1 = never fuse */
+    int32_t fuse_width;         /* narrow-level threshold: the plain sweep runs levels with fewer
+                                   vertices in one CTA between grid barriers; the TMA-staged sweep
+                                   gives them a warp per vertex.  0 = auto, -1 = never */
     int32_t use_cuda_graph;     /* 1 = capture the launch sequence once per workspace and replay */
     int64_t barrier_timeout_ns; /* give up a grid barrier after this long; 0 = 2 s */
     int32_t debug_barrier_extra;/* testing only: the sweep's barriers wait for this many extra
                                    arrivals that never come, so every wait times out */
-    int32_t reserved[7];        /* must be zero */
+    int32_t sweep_kernel;       /* 0 = auto (TMA-staged arc blocks), 1 = TMA-staged, 2 = plain loads */
+    int32_t record_trace;       /* 1 = record the device time of every sweep step (iso_workspace_trace) */
+    int32_t reserved[5];        /* must be zero */
 } iso_query_opts;
 
 /* Answer k isochrone queries (source sources[i], limit taus[i]) in sweeps of
@@ -182,6 +185,14 @@ int iso_collect(iso_workspace* ws, int64_t* out_offsets, int32_t* out_arcs, int6
 /* Per-phase device times of the last collected batch in milliseconds:
  * [0] upward search, [1] sweep, [2] emission, [3] sort + gather. */
 int iso_workspace_timings(const iso_workspace* ws, float* ms4);
+/* Per-level times of the last collected batch (workspaces created with
+ * record_trace = 1 and the TMA-staged sweep).  Entry i < L: steps4[4i..4i+3] =
+ * {0, i, i+1, 0} and ns[i] = device nanoseconds from the start of the level walk
+ * until level block i was complete (blocks in sweep order, block 0 = top level).
+ * Entry L: steps4 = {2, 0, 0, 0} and ns[L] = time spent loading the upward
+ * labels before the walk.  Returns L+1 (at most cap entries are written) or -1
+ * on error. */
+int32_t iso_workspace_trace(const iso_workspace* ws, int32_t* steps4, int64_t* ns, int32_t cap);
 void iso_free_workspace(iso_workspace* ws);
 
 /* ---------------------------------------------------------------------------

@@ -63,7 +63,8 @@ class QueryOpts(ctypes.Structure):
     _fields_ = [("threads_per_vertex", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("fuse_width", ctypes.c_int32), ("use_cuda_graph", ctypes.c_int32),
                 ("barrier_timeout_ns", ctypes.c_int64), ("debug_barrier_extra", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("sweep_kernel", ctypes.c_int32), ("record_trace", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 _lib = None
@@ -87,6 +88,7 @@ EXPORTS = {
     "iso_workspace_timings": (I32, [VP, VP]),
     "iso_free_workspace": (None, [VP]),
     "iso_query_noalloc": (I32, [VP, I32, VP, VP, VP, VP, I64, VP]),
+    "iso_workspace_trace": (I32, [VP, VP, VP, I32]),
     "iso_last_error": (ctypes.c_char_p, []),
     "iso_version": (ctypes.c_char_p, []),
 }
@@ -348,6 +350,16 @@ class Workspace:
         cap = cap if cap is not None else int(out_arcs.numel())
         _check(lib().iso_collect(self._h, _ptr(out_offsets), _ptr(out_arcs), cap, _ptr(out_dist)))
         return out_offsets, out_arcs, out_dist
+
+    def trace(self):
+        """(steps int32[S,4], ns int64[S]) of the last batch (record_trace=1)."""
+        cnt = lib().iso_workspace_trace(self._h, None, None, 0)
+        if cnt < 0:
+            raise IsoError(ISO_E_INVAL, lib().iso_last_error().decode())
+        steps = np.zeros((max(cnt, 1), 4), np.int32)
+        ns = np.zeros(max(cnt, 1), np.int64)
+        lib().iso_workspace_trace(self._h, steps.ctypes.data, ns.ctypes.data, cnt)
+        return steps[:cnt], ns[:cnt]
 
     def timings(self):
         t = (ctypes.c_float * 4)()

@@ -77,6 +77,23 @@ int lanes_class(int k) {
 
 int default_tpv(int K) { return K <= 8 ? 1 : K / 8; }
 
+// Sweep kernel, threads per vertex, CTAs per SM and vertices per CTA batch that
+// options o select for K lanes.  Returns false if the combination is unsupported.
+bool sweep_shape(int K, const iso_query_opts& o, int* kernel, int* tpv, int* occ, int* vpb) {
+    *kernel = o.sweep_kernel == 2 ? 2 : 1;
+    *tpv = o.threads_per_vertex ? o.threads_per_vertex : default_tpv(K);
+    int block = 0;
+    if (*kernel == 1) {
+        if (!iso_sweep_tma_supported(K, *tpv)) return false;
+        *occ = iso_sweep_tma_occupancy(K, *tpv, &block, vpb);
+    } else {
+        if (!iso_sweep_supported(K, *tpv)) return false;
+        *occ = iso_sweep_occupancy(K, *tpv, &block);
+        *vpb = block / *tpv;
+    }
+    return *occ > 0;
+}
+
 }  // namespace
 
 struct iso_graph {
@@ -113,6 +130,12 @@ struct iso_graph {
 struct iso_workspace {
     iso_graph* g = nullptr;
     int K = 0, tpv = 0, grid = 0, fuse_width = 0;
+    int kernel = 1;              // 1 = TMA-staged sweep, 2 = plain loads
+    int narrow_width = 0;        // TMA sweep: levels narrower than this use a warp per vertex
+    bool record_trace = false;
+    long long* trace = nullptr;  // device [nsched + 1]
+    std::vector<long long> h_trace;
+    std::vector<int4> h_sched;
     bool use_graph = false;
     long long timeout_ns = 2000000000LL;
     int bar_extra = 0;
@@ -122,7 +145,11 @@ struct iso_workspace {
     void* mask = nullptr;
     uint8_t* upflag = nullptr;
     int32_t* io = nullptr;       // src[K], tau[K]
-    int32_t* ctl = nullptr;      // status[4], bar[2], pad[2], ecnt[K], upcnt[K]
+    int32_t* ctl = nullptr;      // status[4], bar[2], pad[2], ecnt[K], upcnt[K], level_done[L]
+    int32_t* chunk_off = nullptr;  // [L+1] TMA sweep: first chunk of every level block
+    int32_t* level_mode = nullptr; // [L] TMA sweep: 1 = a warp per vertex
+    unsigned long long* upmask = nullptr;  // [n] TMA sweep: lanes with upward labels
+    int vpb = 0;
     int2* pairs = nullptr;
     uint32_t* gtab = nullptr;
     int gcap = 1 << 14;
@@ -153,7 +180,8 @@ struct iso_workspace {
     uint32_t* bar() { return (uint32_t*)(ctl + 4); }
     int32_t* ecnt() { return ctl + 8; }
     int32_t* upcnt() { return ctl + 8 + K; }
-    size_t ctl_words() const { return 8 + 2 * (size_t)K; }
+    uint32_t* level_done() { return (uint32_t*)(ctl + 8 + 2 * K); }
+    size_t ctl_words() const { return 8 + 2 * (size_t)K + (size_t)g->L; }
 
     void* alloc(size_t bytes) {
         void* p = g->A.get(bytes, stream);
@@ -190,17 +218,32 @@ int build_schedule(iso_workspace* ws) {
         }
     }
     ws->nsched = (int)steps.size();
+    ws->h_sched = steps;
     ws->sched = (int4*)ws->alloc(steps.size() * sizeof(int4));
     if (!ws->sched) { iso::set_error("workspace: device allocation failed"); return ISO_E_NOMEM; }
     ISO_CK(cudaMemcpyAsync(ws->sched, steps.data(), steps.size() * sizeof(int4), cudaMemcpyHostToDevice,
                            ws->stream));
+    // TMA sweep: levels narrower than one chunk per CTA get a warp per vertex
+    std::vector<int32_t> co((size_t)g->L + 1, 0), mode((size_t)g->L, 0);
+    const int narrow_chunk = 31;  // consumer warps per CTA
+    for (int j = 0; j < g->L; ++j) {
+        const int w = g->h_level_off[j + 1] - g->h_level_off[j];
+        mode[j] = ws->narrow_width > 0 && w < ws->narrow_width ? 1 : 0;
+        const int per = mode[j] ? narrow_chunk : ws->vpb;
+        co[j + 1] = co[j] + (w + per - 1) / per;
+    }
+    ws->chunk_off = (int32_t*)ws->alloc(co.size() * 4);
+    ws->level_mode = (int32_t*)ws->alloc(mode.size() * 4);
+    if (!ws->chunk_off || !ws->level_mode) { iso::set_error("workspace: device allocation failed"); return ISO_E_NOMEM; }
+    ISO_CK(cudaMemcpyAsync(ws->chunk_off, co.data(), co.size() * 4, cudaMemcpyHostToDevice, ws->stream));
+    ISO_CK(cudaMemcpyAsync(ws->level_mode, mode.data(), mode.size() * 4, cudaMemcpyHostToDevice, ws->stream));
     ISO_CK(cudaStreamSynchronize(ws->stream));
     return ISO_OK;
 }
 
 int alloc_up(iso_workspace* ws) {
     ws->pairs = (int2*)ws->alloc((size_t)ws->K * ws->gcap * sizeof(int2));
-    ws->gtab = (uint32_t*)ws->alloc((size_t)ws->K * 5 * ws->gcap * sizeof(uint32_t));
+    ws->gtab = (uint32_t*)ws->alloc((size_t)ws->K * iso_upward_table_words(ws->gcap) * sizeof(uint32_t));
     if (!ws->pairs || !ws->gtab) { iso::set_error("workspace: device allocation failed"); return ISO_E_NOMEM; }
     return ISO_OK;
 }
@@ -232,6 +275,8 @@ int enqueue(iso_workspace* ws, bool want_dist, bool capturing) {
     up.src = ws->src(); up.tau = ws->tau();
     up.pairs = ws->pairs; up.cnt = ws->upcnt(); up.gtab = ws->gtab; up.status = ws->status();
     up.n = g->n; up.cap = ws->gcap; up.gcap = ws->gcap; up.tau_max = g->tau_max;
+    up.direct = ws->kernel == 1 ? 1 : 0;
+    up.K = K; up.d = ws->d; up.upmask = ws->upmask; up.upflag = ws->upflag;
     ISO_CK(iso_launch_upward(up, K, s));
     ISO_CK(record(ws->ev[1], s, capturing));
 
@@ -241,7 +286,13 @@ int enqueue(iso_workspace* ws, bool want_dist, bool capturing) {
     sw.d = ws->d; sw.mask = ws->mask; sw.upflag = ws->upflag; sw.bar = ws->bar(); sw.status = ws->status();
     sw.timeout_ns = ws->timeout_ns; sw.n = g->n; sw.L = g->L; sw.nsched = ws->nsched; sw.cap = ws->gcap;
     sw.last_level_block = g->L - 1; sw.write_all = want_dist ? 1 : 0; sw.bar_extra = ws->bar_extra;
-    ISO_CK(iso_launch_sweep(sw, K, ws->tpv, ws->grid, s));
+    sw.trace = ws->trace;
+    sw.chunk_off = ws->chunk_off;
+    sw.level_mode = ws->level_mode;
+    sw.level_done = ws->level_done();
+    sw.upmask = ws->upmask;
+    if (ws->kernel == 1) ISO_CK(iso_launch_sweep_tma(sw, K, ws->tpv, ws->grid, s));
+    else ISO_CK(iso_launch_sweep(sw, K, ws->tpv, ws->grid, s));
     ISO_CK(record(ws->ev[2], s, capturing));
 
     EmitParams em{};
@@ -253,6 +304,8 @@ int enqueue(iso_workspace* ws, bool want_dist, bool capturing) {
     GatherParams ga{};
     ga.ebuf = ws->ebuf; ga.ecnt = ws->ecnt(); ga.tmp = ws->tmp; ga.out = ws->out; ga.out_off = ws->out_off;
     ga.k = K; ga.ecap = ws->ecap;
+    ga.key_bits = 1;
+    while (ga.key_bits < 31 && (int64_t(1) << ga.key_bits) < g->m) ++ga.key_bits;
     ISO_CK(iso_launch_sort_gather(ga, K, s));
     if (want_dist) {
         DistParams dp{};
@@ -335,15 +388,16 @@ extern "C" int iso_upload_graph(const iso_ch* ch, const iso_alloc* alloc, void* 
     g->tau_max = 0x7FFFFFFE - ch->max_w;
     g->h_level_off = ch->level_off;
     const size_t n = (size_t)ch->n;
-    std::vector<uint32_t> off32(n + 1);
+    std::vector<uint32_t> off32(n + 5);  // four spare entries keep 16-byte bulk copies in bounds
     std::vector<int2> arcs;
     int rc = ISO_OK;
     auto free_all = [&]() { for (void* p : g->owned) g->A.put(p, g->stream); g->owned.clear(); };
     for (size_t i = 0; i <= n; ++i) off32[i] = (uint32_t)ch->down_off[i];
+    for (size_t i = n + 1; i < n + 5; ++i) off32[i] = off32[n];
     arcs.resize(ch->down_src.size() + 2);  // two spare entries keep 16-byte loads in bounds
     for (size_t i = 0; i < ch->down_src.size(); ++i) arcs[i] = make_int2(ch->down_src[i], ch->down_w[i]);
     arcs[arcs.size() - 1] = arcs[arcs.size() - 2] = make_int2(0, 0);
-    if ((rc = g->upload(&g->down_off, off32.data(), n + 1)) || (rc = g->upload(&g->down_arc, arcs.data(), arcs.size()))) {
+    if ((rc = g->upload(&g->down_off, off32.data(), n + 5)) || (rc = g->upload(&g->down_arc, arcs.data(), arcs.size()))) {
         free_all(); return rc;
     }
     ISO_CK(cudaStreamSynchronize(g->stream));
@@ -390,18 +444,20 @@ extern "C" int iso_workspace_create(iso_graph* g, int32_t lanes, const iso_query
     ws->g = g;
     ws->stream = (cudaStream_t)stream;
     ws->K = lanes_class(lanes);
-    ws->tpv = (opts && opts->threads_per_vertex) ? opts->threads_per_vertex : default_tpv(ws->K);
-    if (!iso_sweep_supported(ws->K, ws->tpv)) {
-        iso::set_error("iso_workspace_create: %d threads per vertex unsupported for %d lanes", ws->tpv, ws->K);
+    const iso_query_opts o = opts ? *opts : iso_query_opts{};
+    int occ = 0, vpb = 0;
+    if (o.sweep_kernel < 0 || o.sweep_kernel > 2 || !sweep_shape(ws->K, o, &ws->kernel, &ws->tpv, &occ, &vpb)) {
+        iso::set_error("iso_workspace_create: sweep kernel %d with %d threads per vertex unsupported for %d lanes",
+                       o.sweep_kernel, o.threads_per_vertex, ws->K);
         return ISO_E_INVAL;
     }
-    int block = 0;
-    int occ = iso_sweep_occupancy(ws->K, ws->tpv, &block);
-    if (occ <= 0) { iso::set_error("iso_workspace_create: sweep kernel cannot be resident"); return ISO_E_CUDA; }
-    const int per_sm = (opts && opts->ctas_per_sm) ? std::min<int>(opts->ctas_per_sm, occ) : occ;
+    const int per_sm = o.ctas_per_sm ? std::min<int>(o.ctas_per_sm, occ) : occ;
     ws->grid = g->num_sms * per_sm;
-    const int vpb = block / ws->tpv;
-    ws->fuse_width = !opts || opts->fuse_width == 0 ? vpb : (opts->fuse_width < 0 ? 0 : opts->fuse_width);
+    ws->fuse_width = o.fuse_width == 0 ? vpb : (o.fuse_width < 0 ? 0 : o.fuse_width);
+    ws->vpb = vpb;
+    // a level narrower than one chunk of ws->vpb vertices per CTA runs with a warp per vertex
+    ws->narrow_width = o.fuse_width < 0 ? 0 : (o.fuse_width > 0 ? o.fuse_width : ws->grid * vpb);
+    ws->record_trace = o.record_trace != 0 && ws->kernel == 1;
     ws->use_graph = opts ? opts->use_cuda_graph != 0 : false;
     if (opts && opts->barrier_timeout_ns) ws->timeout_ns = opts->barrier_timeout_ns;
     ws->bar_extra = opts ? opts->debug_barrier_extra : 0;
@@ -426,6 +482,11 @@ extern "C" int iso_workspace_create(iso_graph* g, int32_t lanes, const iso_query
         return fail(ISO_E_NOMEM);
     }
     if ((rc = alloc_up(ws.get())) || (rc = alloc_emit(ws.get())) || (rc = build_schedule(ws.get()))) return fail(rc);
+    if (ws->record_trace) {
+        ws->trace = (long long*)ws->alloc(((size_t)g->L + 2) * 8);
+        if (!ws->trace) { iso::set_error("iso_workspace_create: device allocation failed"); return fail(ISO_E_NOMEM); }
+        ws->h_trace.assign((size_t)g->L + 2, 0);
+    }
     if (cudaMallocHost(&ws->h_io, 2 * K * 4) != cudaSuccess ||
         cudaMallocHost(&ws->h_ctl, ws->ctl_words() * 4) != cudaSuccess) {
         cudaGetLastError();
@@ -434,6 +495,15 @@ extern "C" int iso_workspace_create(iso_graph* g, int32_t lanes, const iso_query
     }
     for (auto& e : ws->ev)
         if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); iso::set_error("iso_workspace_create: event"); return fail(ISO_E_CUDA); }
+    if (ws->kernel == 1) {
+        ws->upmask = (unsigned long long*)ws->alloc(n * 8);
+        if (!ws->upmask) { iso::set_error("iso_workspace_create: device allocation failed"); return fail(ISO_E_NOMEM); }
+        if (cudaMemsetAsync(ws->upmask, 0, n * 8, ws->stream) != cudaSuccess) {
+            cudaGetLastError();
+            iso::set_error("iso_workspace_create: initialisation failed");
+            return fail(ISO_E_CUDA);
+        }
+    }
     if (cudaMemsetAsync(ws->upflag, 0, n, ws->stream) != cudaSuccess ||
         cudaStreamSynchronize(ws->stream) != cudaSuccess) {
         cudaGetLastError();
@@ -527,6 +597,8 @@ int collect_impl(iso_workspace* ws, int64_t* out_offsets, int32_t* out_arcs, int
         }
         if (int rc = launch_batch(ws, ws->want_dist)) return rc;
     }
+    if (ws->trace)
+        ISO_CK(cudaMemcpy(ws->h_trace.data(), ws->trace, ws->h_trace.size() * 8, cudaMemcpyDeviceToHost));
     float t[4] = {};
     for (int i = 0; i < 4; ++i) cudaEventElapsedTime(&t[i], ws->ev[i], ws->ev[i + 1]);
     for (int i = 0; i < 4; ++i) ws->phase_ms[i] = t[i];
@@ -565,6 +637,27 @@ extern "C" int iso_collect(iso_workspace* ws, int64_t* out_offsets, int32_t* out
     return collect_impl(ws, out_offsets, out_arcs, cap, out_dist);
 }
 
+extern "C" int32_t iso_workspace_trace(const iso_workspace* ws, int32_t* steps4, int64_t* ns, int32_t cap) {
+    iso::clear_error();
+    if (!ws) { iso::set_error("iso_workspace_trace: NULL workspace"); return -1; }
+    if (!ws->trace) {
+        iso::set_error("iso_workspace_trace: workspace created without record_trace or with the plain sweep");
+        return -1;
+    }
+    const int L = ws->g->L;
+    const long long walk0 = ws->h_trace[(size_t)L + 1];
+    for (int32_t i = 0; i <= L && i < cap; ++i) {
+        if (i < L) {
+            if (steps4) { steps4[4 * i] = 0; steps4[4 * i + 1] = i; steps4[4 * i + 2] = i + 1; steps4[4 * i + 3] = 0; }
+            if (ns) ns[i] = ws->h_trace[(size_t)i + 1] - walk0;
+        } else {
+            if (steps4) { steps4[4 * i] = 2; steps4[4 * i + 1] = 0; steps4[4 * i + 2] = 0; steps4[4 * i + 3] = 0; }
+            if (ns) ns[i] = walk0 - ws->h_trace[0];
+        }
+    }
+    return L + 1;
+}
+
 extern "C" int iso_workspace_timings(const iso_workspace* ws, float* ms4) {
     if (!ws || !ms4) return ISO_E_INVAL;
     std::memcpy(ms4, ws->phase_ms, sizeof(ws->phase_ms));
@@ -574,15 +667,14 @@ extern "C" int iso_workspace_timings(const iso_workspace* ws, float* ms4) {
 namespace {
 // Does workspace ws run with the settings that options o ask for?
 bool same_config(const iso_workspace* ws, const iso_query_opts& o) {
-    const int tpv = o.threads_per_vertex ? o.threads_per_vertex : default_tpv(ws->K);
-    int block = 0;
-    const int occ = iso_sweep_occupancy(ws->K, tpv, &block);
+    int kernel = 0, tpv = 0, occ = 0, vpb = 0;
+    if (!sweep_shape(ws->K, o, &kernel, &tpv, &occ, &vpb)) return false;
     const int per_sm = o.ctas_per_sm ? std::min<int>(o.ctas_per_sm, occ) : occ;
-    const int fuse = o.fuse_width == 0 ? block / std::max(tpv, 1) : (o.fuse_width < 0 ? 0 : o.fuse_width);
+    const int fuse = o.fuse_width == 0 ? vpb : (o.fuse_width < 0 ? 0 : o.fuse_width);
     const long long timeout = o.barrier_timeout_ns ? o.barrier_timeout_ns : 2000000000LL;
-    return ws->tpv == tpv && ws->grid == ws->g->num_sms * per_sm && ws->fuse_width == fuse &&
-           ws->use_graph == (o.use_cuda_graph != 0) && ws->timeout_ns == timeout &&
-           ws->bar_extra == o.debug_barrier_extra;
+    return ws->kernel == kernel && ws->tpv == tpv && ws->grid == ws->g->num_sms * per_sm &&
+           ws->fuse_width == fuse && ws->use_graph == (o.use_cuda_graph != 0) && ws->timeout_ns == timeout &&
+           ws->bar_extra == o.debug_barrier_extra && ws->record_trace == (o.record_trace != 0);
 }
 }  // namespace
 
@@ -641,6 +733,7 @@ extern "C" int iso_query(iso_graph* g, int32_t k, const int32_t* sources, const 
 // Read-only view of a device graph for the allocation-free entry point.
 struct iso_graph_view {
     int n, L, tau_max, num_sms;
+    int64_t m;
     const uint32_t *down_off, *up_off, *orig_off;
     const int2 *down_arc, *up_arc;
     const int32_t *orig_head, *orig_id, *pos, *level_off;
@@ -649,7 +742,7 @@ struct iso_graph_view {
 
 int iso_graph_view_of(const iso_graph* g, iso_graph_view* v) {
     if (!g || !v) return ISO_E_INVAL;
-    v->n = g->n; v->L = g->L; v->tau_max = g->tau_max; v->num_sms = g->num_sms;
+    v->n = g->n; v->L = g->L; v->tau_max = g->tau_max; v->num_sms = g->num_sms; v->m = g->m;
     v->down_off = g->down_off; v->up_off = g->up_off; v->orig_off = g->orig_off;
     v->down_arc = g->down_arc; v->up_arc = g->up_arc;
     v->orig_head = g->orig_head; v->orig_id = g->orig_id; v->pos = g->pos; v->level_off = g->level_off;

@@ -6,6 +6,7 @@
 //   mask[v]         K-bit word, bit i set iff v is in range for lane i.
 //   upflag[v]       1 while d[v*K..] holds upward-search labels not yet consumed
 //                   by the sweep (the sweep clears it).
+//   upmask[v]       lanes whose slot of d[v*K..] holds an upward label (TMA sweep).
 //   down arcs       int2 {src, len} grouped by head, heads in sweep order.
 #pragma once
 
@@ -36,12 +37,19 @@ struct UpParams {
     const int32_t* tau;       // [K]
     int2* pairs;              // [K * cap] {vertex, label} per lane
     int32_t* cnt;             // [K]
-    uint32_t* gtab;           // [K * 3 * gcap] global fallback tables
+    uint32_t* gtab;           // [K * iso_upward_table_words(gcap)] global fallback tables
     int32_t* status;
     int n;
     int cap;                  // entries per lane in pairs (== gcap)
     int gcap;                 // power of two
     int tau_max;
+    // direct != 0: instead of pairs, write every label into its row slot d[v*K + lane],
+    // set bit lane of upmask[v] and upflag[v] (the TMA sweep reads them there)
+    int direct;
+    int K;
+    uint32_t* d;
+    unsigned long long* upmask;
+    uint8_t* upflag;
 };
 
 struct SweepParams {
@@ -62,6 +70,11 @@ struct SweepParams {
     int last_level_block;      // index j of the lowest level (its d rows need no store)
     int write_all;             // store every d row (distances requested)
     int bar_extra;             // testing: extra arrivals a barrier waits for
+    long long* trace;          // nullable: global ns; layout depends on the kernel (see iso_api.cu)
+    const int32_t* chunk_off;  // [L+1] first chunk of every level block (TMA kernel)
+    const int32_t* level_mode; // [L] 0: a thread group per vertex, 1: a warp per vertex (TMA kernel)
+    uint32_t* level_done;      // [L] chunks completed per level block (TMA kernel), zeroed per batch
+    unsigned long long* upmask;// [n] lanes with an upward label (TMA kernel)
 };
 
 struct EmitParams {
@@ -101,9 +114,13 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 // Launchers (one translation unit each); return the launch's cudaError_t.
 cudaError_t iso_launch_upward(const isod::UpParams& p, int K, cudaStream_t s);
+size_t iso_upward_table_words(size_t gcap);  // 32-bit words of one lane's global table
 cudaError_t iso_launch_sweep(const isod::SweepParams& p, int K, int tpv, int grid, cudaStream_t s);
 int iso_sweep_occupancy(int K, int tpv, int* block);
 bool iso_sweep_supported(int K, int tpv);
+cudaError_t iso_launch_sweep_tma(const isod::SweepParams& p, int K, int tpv, int grid, cudaStream_t s);
+int iso_sweep_tma_occupancy(int K, int tpv, int* block, int* vpb);
+bool iso_sweep_tma_supported(int K, int tpv);
 cudaError_t iso_launch_emit(const isod::EmitParams& p, int K, int grid, cudaStream_t s);
 cudaError_t iso_launch_sort_gather(const isod::GatherParams& p, int K, cudaStream_t s);
 cudaError_t iso_launch_dist(const isod::DistParams& p, cudaStream_t s);

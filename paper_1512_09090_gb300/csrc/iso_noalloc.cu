@@ -88,6 +88,7 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 // Fields of iso_graph needed here (the struct is defined in iso_api.cu).
 struct iso_graph_view {
     int n, L, tau_max, num_sms;
+    int64_t m;
     const uint32_t *down_off, *up_off, *orig_off;
     const int2 *down_arc, *up_arc;
     const int32_t *orig_head, *orig_id, *pos, *level_off;
@@ -192,6 +193,8 @@ extern "C" int iso_query_noalloc(iso_graph* g, int32_t k, const int32_t* sources
     GatherParams ga{};
     ga.ebuf = em.ebuf; ga.ecnt = em.ecnt; ga.tmp = (int32_t*)(base + kOffTmp); ga.out = (int32_t*)(base + kOffOut);
     ga.out_off = (int64_t*)(base + kOffOutOff); ga.k = kLanes; ga.ecap = kMaxArcs;
+    ga.key_bits = 1;
+    while (ga.key_bits < 31 && (int64_t(1) << ga.key_bits) < gv.m) ++ga.key_bits;
     if ((e = iso_launch_sort_gather(ga, kLanes, stream)) != cudaSuccess)
         return fail(ISO_E_CUDA, "sort launch", e);
 

@@ -22,7 +22,7 @@ template <> struct MaskOf<64> { using T = unsigned long long; };
 
 constexpr int kEmitThreads = 256;
 constexpr int kSortThreads = 1024;
-constexpr int kSortSmem = 32768;  // ids sorted in shared memory (128 KB)
+constexpr int kSortSmem = 32768;  // ids bucketed in shared memory (128 KB)
 
 __device__ __forceinline__ unsigned long long warp_or(unsigned long long x) {
     const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)x);
@@ -34,21 +34,30 @@ template <int K>
 __global__ void __launch_bounds__(kEmitThreads) k_emit(EmitParams p) {
     using MaskT = typename MaskOf<K>::T;
     const MaskT* mask = static_cast<const MaskT*>(p.mask);
-    const unsigned lane_id = threadIdx.x & 31;
-    const unsigned lt = (1u << lane_id) - 1u;
-    for (int base = blockIdx.x * blockDim.x; base < p.n; base += gridDim.x * blockDim.x) {
-        const int u = base + threadIdx.x;
-        unsigned long long mu = 0;
-        uint32_t a = 0, e = 0;
-        if (u < p.n) {
-            mu = mask[u];
-            a = __ldg(p.orig_off + u);
-            e = __ldg(p.orig_off + u + 1);
-        }
-        for (; __any_sync(0xffffffffu, a < e); ++a) {
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int warps = (int)(gridDim.x * blockDim.x) >> 5;
+    // a warp takes 32 consecutive tails; their arcs are one contiguous range
+    for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w * 32 < p.n; w += warps) {
+        const int u0 = w * 32;
+        const int u = min(u0 + (int)lane, p.n);
+        const uint32_t my_off = __ldg(p.orig_off + u);           // start of tail u0+lane's arcs
+        const uint32_t a0 = __shfl_sync(0xffffffffu, my_off, 0);
+        const uint32_t a1 = __ldg(p.orig_off + min(u0 + 32, p.n));
+        const unsigned long long mu_lane = u < p.n ? (unsigned long long)mask[u] : 0ull;
+        for (uint32_t base = a0; base < a1; base += 32) {
+            const uint32_t a = base + lane;
             unsigned long long x = 0;
             int id = 0;
-            if (a < e) {
+            // tail of arc a: the last lane t whose first arc is <= a
+            int lo = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const uint32_t o = __shfl_sync(0xffffffffu, my_off, lo + step);
+                if (lo + step < 32 && o <= a) lo += step;
+            }
+            const unsigned long long mu = __shfl_sync(0xffffffffu, mu_lane, lo);
+            if (a < a1) {
                 x = mu ^ (unsigned long long)mask[__ldg(p.orig_head + a)];
                 if (x) id = __ldg(p.orig_id + a);
             }
@@ -60,7 +69,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(EmitParams p) {
                 const unsigned b = __ballot_sync(0xffffffffu, (x >> i) & 1ull);
                 const int leader = __ffs(b) - 1;
                 int at = 0;
-                if ((int)lane_id == leader) at = atomicAdd(p.ecnt + i, __popc(b));
+                if ((int)lane == leader) at = atomicAdd(p.ecnt + i, __popc(b));
                 at = __shfl_sync(0xffffffffu, at, leader);
                 if ((x >> i) & 1ull) {
                     const int q = at + __popc(b & lt);
@@ -88,14 +97,27 @@ __device__ void bitonic(int32_t* s, int n2) {
     }
 }
 
+// One CTA per lane.  Ids are distinct and below 2^key_bits, so the list is
+// split by its top bits into about cnt/4 buckets (histogram, scan, scatter);
+// buckets are then sorted on their own: small ones by one thread each
+// (insertion sort), any bucket above kSmallBucket ids by the whole CTA
+// (bitonic network in the lane's global scratch).  Concatenated buckets are
+// the sorted list.  CTA 0 also writes the offsets of all lanes.
+constexpr int kMaxBuckets = 8192;
+constexpr int kSmallBucket = 64;
+
 __global__ void __launch_bounds__(kSortThreads) k_sort_gather(GatherParams p) {
     extern __shared__ int32_t sbuf[];
-    const int lane = blockIdx.x;
+    int32_t* s_hist = sbuf + kSortSmem;           // [kMaxBuckets + 1]
+    int32_t* s_cur = s_hist + kMaxBuckets + 1;    // [kMaxBuckets]
     __shared__ long long s_off;
+    __shared__ int s_nbig, s_big[256];
+    const int lane = blockIdx.x;
     if (threadIdx.x == 0) {
         long long off = 0;
         for (int i = 0; i < lane; ++i) off += min(p.ecnt[i], p.ecap);
         s_off = off;
+        s_nbig = 0;
         if (lane == 0) {
             long long o = 0;
             p.out_off[0] = 0;
@@ -106,15 +128,88 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_gather(GatherParams p) {
     if (lane >= p.k) return;
     const int cnt = min(p.ecnt[lane], p.ecap);
     if (cnt == 0) return;
-    int n2 = 1;
-    while (n2 < cnt) n2 <<= 1;
     const int32_t* seg = p.ebuf + (size_t)lane * p.ecap;
-    int32_t* s = n2 <= kSortSmem ? sbuf : p.tmp + (size_t)lane * p.ecap;
-    for (int i = threadIdx.x; i < n2; i += blockDim.x) s[i] = i < cnt ? seg[i] : INT32_MAX;
-    __syncthreads();
-    bitonic(s, n2);
+    int32_t* tmp = p.tmp + (size_t)lane * p.ecap;
     int32_t* out = p.out + s_off;
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) out[i] = s[i];
+    int32_t* B = cnt <= kSortSmem ? sbuf : tmp;     // bucketed copy of the list
+    int lg = 0;
+    while ((1 << lg) < kMaxBuckets && (4 << lg) < cnt) ++lg;
+    const int nb = 1 << lg;
+    const int shift = max(0, p.key_bits - lg);
+    for (int b = threadIdx.x; b <= nb; b += blockDim.x) s_hist[b] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) atomicAdd(&s_hist[min(seg[i] >> shift, nb - 1)], 1);
+    __syncthreads();
+    // exclusive scan of the nb counts (nb <= 8192 = 8 per thread)
+    {
+        __shared__ int s_part[kSortThreads];
+        const int per = (nb + blockDim.x - 1) / blockDim.x;
+        const int b0 = threadIdx.x * per;
+        int sum = 0;
+        for (int b = b0; b < min(b0 + per, nb); ++b) sum += s_hist[b];
+        s_part[threadIdx.x] = sum;
+        __syncthreads();
+        for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+            const int v = threadIdx.x >= (unsigned)o ? s_part[threadIdx.x - o] : 0;
+            __syncthreads();
+            s_part[threadIdx.x] += v;
+            __syncthreads();
+        }
+        int acc = s_part[threadIdx.x] - sum;
+        for (int b = b0; b < min(b0 + per, nb); ++b) {
+            const int c = s_hist[b];
+            s_hist[b] = acc;
+            s_cur[b] = acc;
+            acc += c;
+        }
+        if (threadIdx.x == 0) s_hist[nb] = cnt;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const int32_t x = seg[i];
+        B[atomicAdd(&s_cur[min(x >> shift, nb - 1)], 1)] = x;
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        const int lo = s_hist[b], hi = s_hist[b + 1];
+        if (hi - lo > kSmallBucket) {
+            const int q = atomicAdd(&s_nbig, 1);
+            if (q < 256) s_big[q] = b;
+            continue;
+        }
+        for (int i = lo + 1; i < hi; ++i) {
+            const int32_t x = B[i];
+            int j = i - 1;
+            while (j >= lo && B[j] > x) { B[j + 1] = B[j]; --j; }
+            B[j + 1] = x;
+        }
+    }
+    __syncthreads();
+    const int nbig = s_nbig;
+    if (nbig > 256) {
+        // too many large buckets: sort the whole list with one network in scratch
+        int n2 = 1;
+        while (n2 < cnt) n2 <<= 1;
+        int32_t* g = const_cast<int32_t*>(seg);
+        for (int i = threadIdx.x; i < n2; i += blockDim.x) g[i] = i < cnt ? B[i] : INT32_MAX;
+        __syncthreads();
+        bitonic(g, n2);
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) out[i] = g[i];
+        return;
+    }
+    for (int t = 0; t < nbig; ++t) {
+        const int b = s_big[t];
+        const int lo = s_hist[b], c = s_hist[b + 1] - lo;
+        int n2 = 1;
+        while (n2 < c) n2 <<= 1;
+        int32_t* g = const_cast<int32_t*>(seg);     // the input list is no longer needed
+        for (int i = threadIdx.x; i < n2; i += blockDim.x) g[i] = i < c ? B[lo + i] : INT32_MAX;
+        __syncthreads();
+        bitonic(g, n2);
+        for (int i = threadIdx.x; i < c; i += blockDim.x) B[lo + i] = g[i];
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) out[i] = B[i];
 }
 
 __global__ void k_dist(DistParams p) {
@@ -141,7 +236,7 @@ cudaError_t iso_launch_emit(const isod::EmitParams& p, int K, int grid, cudaStre
 }
 
 cudaError_t iso_launch_sort_gather(const isod::GatherParams& p, int K, cudaStream_t s) {
-    const int smem = kSortSmem * 4;
+    const int smem = (kSortSmem + 2 * kMaxBuckets + 1) * 4;
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_sort_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

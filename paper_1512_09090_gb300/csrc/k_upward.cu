@@ -5,58 +5,73 @@
 // One CTA per lane.  Every upward arc ends at a strictly higher CH level, so
 // G_up is a DAG and a frontier-based Bellman-Ford over it converges after as
 // many rounds as the longest shortest upward path has arcs: each round relaxes
-// the out-arcs of every vertex whose label improved in the previous round.
-// Labels live in an open-addressing hash table in shared memory (vertex ->
-// label); a search space too large for it is redone with a table in global
-// memory.  Dropping labels above tau is exact because lengths are non-negative:
-// every prefix of a path of length <= tau is itself <= tau.
+// the out-arcs of every vertex whose label improved in the previous round.  A
+// warp takes one frontier vertex at a time and spreads its arcs over its 32
+// threads.  Labels live in an open-addressing hash table in shared memory
+// (vertex -> label) with a bitmap of the vertices queued for the next round; a
+// search space too large for it is redone with the same structures in global
+// memory.  Dropping labels above tau is exact because lengths are
+// non-negative: every prefix of a path of length <= tau is itself <= tau.
 #include "iso_device.cuh"
 
 namespace {
 
 using namespace isod;
 
-constexpr int kThreads = 512;
-constexpr int kSmemSlots = 8192;  // power of two
+constexpr int kThreads = 1024;
+constexpr int kSmemSlots = 16384;  // power of two; at most half of them occupied
 
 struct Table {
-    int32_t* key;     // vertex or -1
-    uint32_t* dist;   // label
-    int32_t* stamp;   // last round in which the slot was queued
-    int32_t* fr[2];   // frontier slot lists
-    uint32_t mask;    // slots - 1
-    int limit;        // maximum occupied slots before giving up
+    int32_t* key;      // vertex or -1
+    uint32_t* dist;    // label
+    uint32_t* queued;  // bitmap: slot is in the next frontier
+    int32_t* fr[2];    // frontier slot lists, capacity = limit
+    uint32_t mask;     // slots - 1
+    int limit;         // maximum occupied slots
 };
+
+__host__ __device__ constexpr size_t table_words(size_t slots) {
+    return slots + slots + slots / 32 + slots;  // key, dist, queued bits, two half-size frontiers
+}
 
 __device__ __forceinline__ int find_or_insert(const Table& t, int32_t v, int* s_used) {
     uint32_t s = ((uint32_t)v * 0x9E3779B1u) & t.mask;
     for (uint32_t probe = 0; probe <= t.mask; ++probe) {
-        int32_t k = atomicCAS(&t.key[s], -1, v);
+        const int32_t k = atomicCAS(&t.key[s], -1, v);
         if (k == v) return (int)s;
-        if (k == -1) {
-            if (atomicAdd(s_used, 1) >= t.limit) return -1;
-            return (int)s;
-        }
+        if (k == -1) return atomicAdd(s_used, 1) < t.limit ? (int)s : -1;
         s = (s + 1) & t.mask;
     }
     return -1;
+}
+
+__device__ __forceinline__ Table carve(uint32_t* base, uint32_t slots) {
+    Table t;
+    t.key = (int32_t*)base;
+    t.dist = base + slots;
+    t.queued = base + 2 * slots;
+    t.fr[0] = (int32_t*)(base + 2 * slots + slots / 32);
+    t.fr[1] = t.fr[0] + slots / 2;
+    t.mask = slots - 1;
+    t.limit = (int)(slots / 2);
+    return t;
 }
 
 // Runs the search with table t.  Returns false if the table overflowed.
 __device__ bool search(const Table& t, const UpParams& p, int32_t s, uint32_t tau, int lane) {
     __shared__ int s_used, s_nfr, s_next, s_over, s_out;
     const uint32_t slots = t.mask + 1;
+    const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     for (uint32_t i = threadIdx.x; i < slots; i += blockDim.x) {
         t.key[i] = -1;
         t.dist[i] = kInf;
-        t.stamp[i] = -1;
     }
+    for (uint32_t i = threadIdx.x; i < slots / 32; i += blockDim.x) t.queued[i] = 0;
     if (threadIdx.x == 0) { s_used = 0; s_over = 0; s_out = 0; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        int sl = find_or_insert(t, s, &s_used);
+        const int sl = find_or_insert(t, s, &s_used);
         t.dist[sl] = 0;
-        t.stamp[sl] = 0;
         t.fr[0][0] = sl;
         s_nfr = 1;
     }
@@ -65,24 +80,24 @@ __device__ bool search(const Table& t, const UpParams& p, int32_t s, uint32_t ta
         const int32_t* cur = t.fr[r & 1];
         int32_t* nxt = t.fr[(r + 1) & 1];
         const int nfr = s_nfr;
+        // a vertex leaves the queue when its round starts; a later improvement re-queues it
+        for (int i = threadIdx.x; i < nfr; i += blockDim.x) atomicAnd(&t.queued[cur[i] >> 5], ~(1u << (cur[i] & 31)));
         if (threadIdx.x == 0) s_next = 0;
         __syncthreads();
-        for (int i = threadIdx.x; i < nfr; i += blockDim.x) {
-            const int su = cur[i];
+        for (int f = warp; f < nfr; f += nwarps) {
+            const int su = cur[f];
             const int32_t u = t.key[su];
             const uint32_t du = *((volatile uint32_t*)&t.dist[su]);
-            for (uint32_t a = p.up_off[u], e = p.up_off[u + 1]; a < e; ++a) {
+            const uint32_t a1 = __ldg(p.up_off + u + 1);
+            for (uint32_t a = __ldg(p.up_off + u) + wl; a < a1; a += 32) {
                 const int2 arc = __ldg(&p.up_arc[a]);
                 const uint32_t nd = du + (uint32_t)arc.y;
                 if (nd > tau) continue;
                 const int sx = find_or_insert(t, arc.x, &s_used);
                 if (sx < 0) { s_over = 1; continue; }
                 if (nd < atomicMin(&t.dist[sx], nd)) {
-                    if (atomicExch(&t.stamp[sx], r + 1) != r + 1) {
-                        int q = atomicAdd(&s_next, 1);
-                        if (q < t.limit) nxt[q] = sx;
-                        else s_over = 1;
-                    }
+                    const uint32_t bit = 1u << (sx & 31);
+                    if (!(atomicOr(&t.queued[sx >> 5], bit) & bit)) nxt[atomicAdd(&s_next, 1)] = sx;
                 }
             }
         }
@@ -91,12 +106,22 @@ __device__ bool search(const Table& t, const UpParams& p, int32_t s, uint32_t ta
         __syncthreads();
     }
     if (s_over) return false;
-    int2* out = p.pairs + (size_t)lane * p.cap;
-    for (uint32_t i = threadIdx.x; i < slots; i += blockDim.x) {
-        const int32_t v = t.key[i];
-        if (v >= 0) {
-            int q = atomicAdd(&s_out, 1);
-            out[q] = make_int2(v, (int)t.dist[i]);
+    if (p.direct) {
+        // labels go straight into their row slots; other lanes own the other slots
+        for (uint32_t i = threadIdx.x; i < slots; i += blockDim.x) {
+            const int32_t v = t.key[i];
+            if (v >= 0) {
+                p.d[(size_t)v * p.K + lane] = t.dist[i];
+                atomicOr(p.upmask + v, 1ull << lane);
+                p.upflag[v] = 1;
+                atomicAdd(&s_out, 1);
+            }
+        }
+    } else {
+        int2* out = p.pairs + (size_t)lane * p.cap;
+        for (uint32_t i = threadIdx.x; i < slots; i += blockDim.x) {
+            const int32_t v = t.key[i];
+            if (v >= 0) out[atomicAdd(&s_out, 1)] = make_int2(v, (int)t.dist[i]);
         }
     }
     __syncthreads();
@@ -105,7 +130,7 @@ __device__ bool search(const Table& t, const UpParams& p, int32_t s, uint32_t ta
 }
 
 __global__ void __launch_bounds__(kThreads) k_upward(UpParams p) {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(16) uint32_t smem[];
     const int lane = blockIdx.x;
     const int32_t src = p.src[lane];
     const int32_t tau = p.tau[lane];
@@ -118,35 +143,22 @@ __global__ void __launch_bounds__(kThreads) k_upward(UpParams p) {
         return;
     }
     const int32_t s = p.pos[src];
-    Table t;
-    t.key = (int32_t*)smem;
-    t.dist = (uint32_t*)(t.key + kSmemSlots);
-    t.stamp = (int32_t*)(t.dist + kSmemSlots);
-    t.fr[0] = t.stamp + kSmemSlots;
-    t.fr[1] = t.fr[0] + kSmemSlots / 2;
-    t.mask = kSmemSlots - 1;
-    t.limit = kSmemSlots / 2;
-    if (search(t, p, s, (uint32_t)tau, lane)) return;
-    // Too large for shared memory: same search on this lane's global table.
-    const size_t g = (size_t)p.gcap;
-    uint32_t* base = p.gtab + (size_t)lane * 5 * g;
-    t.key = (int32_t*)base;
-    t.dist = base + g;
-    t.stamp = (int32_t*)(base + 2 * g);
-    t.fr[0] = (int32_t*)(base + 3 * g);
-    t.fr[1] = (int32_t*)(base + 4 * g);
-    t.mask = (uint32_t)g - 1;
-    t.limit = (int)(g / 2);
+    const bool small_cap = !p.direct && p.cap < kSmemSlots / 2;   // pairs must hold every label
+    if (!small_cap && search(carve(smem, kSmemSlots), p, s, (uint32_t)tau, lane)) return;
+    // Too large for shared memory: the same search on this lane's global table.
     __syncthreads();
-    if (!search(t, p, s, (uint32_t)tau, lane)) {
+    uint32_t* base = p.gtab + (size_t)lane * table_words((size_t)p.gcap);
+    if (!search(carve(base, (uint32_t)p.gcap), p, s, (uint32_t)tau, lane)) {
         if (threadIdx.x == 0) { p.cnt[lane] = 0; atomicCAS(p.status, kStOk, kStUpOverflow); }
     }
 }
 
 }  // namespace
 
+size_t iso_upward_table_words(size_t gcap) { return table_words(gcap); }
+
 cudaError_t iso_launch_upward(const isod::UpParams& p, int K, cudaStream_t s) {
-    const size_t smem = (size_t)kSmemSlots * 4 * 4;  // key, dist, stamp, two half frontiers
+    const size_t smem = table_words(kSmemSlots) * 4;  // 194 KB
     static bool attr = false;
     if (!attr) {
         cudaError_t e = cudaFuncSetAttribute(k_upward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -78,22 +78,52 @@ def test_grid64_lane_counts(k):
     check_batch(g, dg, srcs, taus)
 
 
-@pytest.mark.parametrize("k,tpv", [(8, 2), (16, 1), (16, 2), (16, 4), (32, 1), (32, 2), (32, 4), (32, 8),
-                                   (64, 1), (64, 2), (64, 4), (64, 8), (64, 16)])
-def test_threads_per_vertex_variants(k, tpv):
+PLAIN_VARIANTS = [(8, 2), (16, 1), (16, 2), (16, 4), (32, 1), (32, 2), (32, 4), (32, 8),
+                  (64, 1), (64, 2), (64, 4), (64, 8), (64, 16)]
+TMA_VARIANTS = [(1, 1), (4, 1), (8, 1), (16, 2), (16, 4), (32, 4), (32, 8), (64, 8), (64, 16)]
+
+
+@pytest.mark.parametrize("kernel,k,tpv", [(2, k, t) for k, t in PLAIN_VARIANTS] + [(1, k, t) for k, t in TMA_VARIANTS])
+def test_threads_per_vertex_variants(kernel, k, tpv):
     g, dg = dev_graph("grid64")
     srcs = synth.draw_sources(g, k, 7)
     taus = synth.draw_taus_uniform(k, 300, 3000, 8)
-    check_batch(g, dg, srcs, taus, threads_per_vertex=tpv)
+    check_batch(g, dg, srcs, taus, threads_per_vertex=tpv, sweep_kernel=kernel)
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_both_sweep_kernels_on_grid1k(kernel):
+    g, dg = dev_graph("grid1k")
+    srcs = synth.draw_sources(g, 64, 31)
+    taus = synth.draw_taus_uniform(64, 0, 60000, 32)
+    check_batch(g, dg, srcs, taus, want_dist=True, sweep_kernel=kernel)
+
+
+def test_trace_reports_every_step():
+    g, dg = dev_graph("grid1k")
+    ws = P.Workspace(dg, 16, record_trace=1)
+    ws.submit(synth.draw_sources(g, 16, 3), np.full(16, 20000, np.int32))
+    ws.collect()
+    steps, ns = ws.trace()
+    L = g_levels(dg)
+    assert steps.shape[0] == ns.shape[0] == L + 1
+    assert np.array_equal(steps[:L, 1], np.arange(L)) and steps[L, 0] == 2
+    # a level block completes only after the block above it
+    assert np.all(np.diff(ns[:L]) >= 0) and ns[L - 1] > 0 and ns[L] >= 0
+
+
+def g_levels(dg):
+    return dg.levels
 
 
 @pytest.mark.parametrize("fuse", [-1, 1, 64, 100000])
 @pytest.mark.parametrize("graph", [0, 1])
-def test_fusion_and_cuda_graph(fuse, graph):
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_fusion_and_cuda_graph(fuse, graph, kernel):
     g, dg = dev_graph("grid64")
     srcs = synth.draw_sources(g, 16, 5)
     taus = synth.draw_taus_uniform(16, 0, 3000, 6)
-    check_batch(g, dg, srcs, taus, fuse_width=fuse, use_cuda_graph=graph)
+    check_batch(g, dg, srcs, taus, fuse_width=fuse, use_cuda_graph=graph, sweep_kernel=kernel)
 
 
 def test_duplicate_sources_and_extreme_limits():
@@ -171,12 +201,13 @@ def test_argument_errors_and_recovery():
     check_batch(g, dg, synth.draw_sources(g, 4, 9), np.full(4, 900, np.int32))
 
 
-def test_barrier_timeout_is_reported_and_context_survives():
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_barrier_timeout_is_reported_and_context_survives(kernel):
     g, dg = dev_graph("grid64")
     srcs = synth.draw_sources(g, 4, 2)
     taus = np.full(4, 1000, np.int32)
     with pytest.raises(P.IsoError) as e:
-        P.iso_query(dg, srcs, taus, debug_barrier_extra=1, barrier_timeout_ns=20_000_000)
+        P.iso_query(dg, srcs, taus, debug_barrier_extra=1, barrier_timeout_ns=20_000_000, sweep_kernel=kernel)
     assert e.value.code == P.ISO_E_TIMEOUT
     torch.cuda.synchronize()
     check_batch(g, dg, srcs, taus)
