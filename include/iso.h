@@ -105,6 +105,7 @@ typedef struct {
     const int64_t* orig_off;  /* [n+1] */
     const int32_t* orig_head; /* [m] */
     const int32_t* orig_id;   /* [m] input arc index */
+    const int32_t* bfs;       /* [n] BFS rank of each sweep position in the undirected input graph */
 } iso_ch_view;
 int  iso_ch_view_arrays(const iso_ch* ch, iso_ch_view* out);
 /* Position of original vertex v in sweep order (descending level), or -1. */
@@ -187,8 +188,9 @@ int iso_collect(iso_workspace* ws, int64_t* out_offsets, int32_t* out_arcs, int6
 int iso_workspace_timings(const iso_workspace* ws, float* ms4);
 /* Per-level times of the last collected batch (workspaces created with
  * record_trace = 1 and the TMA-staged sweep).  Entry i < L: steps4[4i..4i+3] =
- * {0, i, i+1, 0} and ns[i] = device nanoseconds from the start of the level walk
- * until level block i was complete (blocks in sweep order, block 0 = top level).
+ * {0, i, i+1, 0} and ns[i] = device nanoseconds from the start of the sweep
+ * until the last chunk of level block i was complete (blocks in sweep order,
+ * block 0 = top level; the sweep interleaves levels, so these need not grow).
  * Entry L: steps4 = {2, 0, 0, 0} and ns[L] = time spent loading the upward
  * labels before the walk.  Returns L+1 (at most cap entries are written) or -1
  * on error. */

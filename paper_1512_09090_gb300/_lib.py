@@ -48,7 +48,8 @@ class ChStats(ctypes.Structure):
 
 class ChView(ctypes.Structure):
     _fields_ = [(k, ctypes.c_void_p) for k in ("perm", "pos", "level_off", "down_off", "down_src", "down_w",
-                                              "up_off", "up_dst", "up_w", "orig_off", "orig_head", "orig_id")]
+                                              "up_off", "up_dst", "up_w", "orig_off", "orig_head", "orig_id",
+                                              "bfs")]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -160,7 +161,7 @@ class CH:
             down_w=arr(v.down_w, np.int32, st.m_down), up_off=arr(v.up_off, np.int64, n + 1),
             up_dst=arr(v.up_dst, np.int32, st.m_up), up_w=arr(v.up_w, np.int32, st.m_up),
             orig_off=arr(v.orig_off, np.int64, n + 1), orig_head=arr(v.orig_head, np.int32, st.m),
-            orig_id=arr(v.orig_id, np.int32, st.m))
+            orig_id=arr(v.orig_id, np.int32, st.m), bfs=arr(v.bfs, np.int32, n))
 
     def save(self, path: str):
         _check(lib().iso_save_ch(self._h, path.encode()))

@@ -482,8 +482,10 @@ extern "C" int iso_build_ch(int32_t n, int64_t m, const int32_t* tail, const int
         for (int32_t p = 0; p < n; ++p) P[order[p]] = p;
         ch->perm.resize(n);
         ch->pos.resize(n);
+        ch->bfs.resize(n);
         for (int32_t p = 0; p < n; ++p) {
             ch->perm[p] = orig_of[order[p]];
+            ch->bfs[p] = order[p];  // internal ids are BFS ranks
             ch->pos[orig_of[order[p]]] = p;
         }
         ch->level_off.assign(L + 1, 0);

@@ -20,6 +20,9 @@ struct iso_ch {
     std::vector<int32_t> pos;        // original vertex id -> sweep position
     // level_off[j] .. level_off[j+1] are the sweep positions of level L-1-j
     std::vector<int32_t> level_off;  // [L+1]
+    // BFS rank (in the undirected input graph) of every sweep position: a
+    // spatial key that orders chunks of different levels for cache locality
+    std::vector<int32_t> bfs;        // [n]
     // incoming downward arcs (u -> v, rank(u) > rank(v)) of each sweep position v,
     // u given as a sweep position (always < v)
     std::vector<int64_t> down_off;   // [n+1]

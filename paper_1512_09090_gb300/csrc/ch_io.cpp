@@ -1,8 +1,8 @@
 // CH file format, array views and the thread-local error message.
 //
-// File layout (little-endian): magic "ISOCH\0\0\1", then int32 n, int32 L,
+// File layout (little-endian): magic "ISOCH\0\0\2", then int32 n, int32 L,
 // int32 max_w, int32 reserved, int64 m, int64 m_down, int64 m_up, int64
-// shortcuts, then the arrays perm, level_off, down_off, down_src, down_w,
+// shortcuts, then the arrays perm, bfs, level_off, down_off, down_src, down_w,
 // up_off, up_dst, up_w, orig_off, orig_head, orig_id in that order.  Loading
 // checks every size and id so a truncated or foreign file is rejected.
 #include <cstdio>
@@ -31,7 +31,7 @@ extern "C" const char* iso_last_error(void) { return iso::g_last_error.c_str(); 
 extern "C" const char* iso_version(void) { return "iso-gb300 0.1 (sm_103a)"; }
 
 namespace {
-const char kMagic[8] = {'I', 'S', 'O', 'C', 'H', 0, 0, 1};
+const char kMagic[8] = {'I', 'S', 'O', 'C', 'H', 0, 0, 2};
 
 template <class T>
 bool put(FILE* f, const std::vector<T>& v) {
@@ -51,6 +51,7 @@ extern "C" int iso_ch_view_arrays(const iso_ch* ch, iso_ch_view* o) {
     o->down_off = ch->down_off.data(); o->down_src = ch->down_src.data(); o->down_w = ch->down_w.data();
     o->up_off = ch->up_off.data(); o->up_dst = ch->up_dst.data(); o->up_w = ch->up_w.data();
     o->orig_off = ch->orig_off.data(); o->orig_head = ch->orig_head.data(); o->orig_id = ch->orig_id.data();
+    o->bfs = ch->bfs.data();
     return ISO_OK;
 }
 
@@ -62,7 +63,7 @@ extern "C" int iso_save_ch(const iso_ch* ch, const char* path) {
     int32_t hdr32[4] = {ch->n, ch->L, ch->max_w, 0};
     int64_t hdr64[4] = {ch->m, ch->down_off.back(), ch->up_off.back(), ch->shortcuts};
     bool ok = std::fwrite(kMagic, 1, 8, f) == 8 && std::fwrite(hdr32, 4, 4, f) == 4 &&
-              std::fwrite(hdr64, 8, 4, f) == 4 && put(f, ch->perm) && put(f, ch->level_off) &&
+              std::fwrite(hdr64, 8, 4, f) == 4 && put(f, ch->perm) && put(f, ch->bfs) && put(f, ch->level_off) &&
               put(f, ch->down_off) && put(f, ch->down_src) && put(f, ch->down_w) &&
               put(f, ch->up_off) && put(f, ch->up_dst) && put(f, ch->up_w) && put(f, ch->orig_off) &&
               put(f, ch->orig_head) && put(f, ch->orig_id);
@@ -104,7 +105,7 @@ extern "C" int iso_load_ch(const char* path, iso_ch** out) {
              mu >= 0 && md <= (int64_t)UINT32_MAX && mu <= (int64_t)UINT32_MAX && ch->max_w >= 0 &&
              ch->max_w <= iso::kMaxWeight;
         size_t n = (size_t)ch->n;
-        ok = ok && get(f, ch->perm, n) && get(f, ch->level_off, (size_t)ch->L + 1) &&
+        ok = ok && get(f, ch->perm, n) && get(f, ch->bfs, n) && get(f, ch->level_off, (size_t)ch->L + 1) &&
              get(f, ch->down_off, n + 1) && get(f, ch->down_src, (size_t)md) && get(f, ch->down_w, (size_t)md) &&
              get(f, ch->up_off, n + 1) && get(f, ch->up_dst, (size_t)mu) && get(f, ch->up_w, (size_t)mu) &&
              get(f, ch->orig_off, n + 1) && get(f, ch->orig_head, (size_t)ch->m) &&
@@ -112,7 +113,7 @@ extern "C" int iso_load_ch(const char* path, iso_ch** out) {
         char extra;
         ok = ok && std::fread(&extra, 1, 1, f) == 0;
         ok = ok && offsets_ok(ch->down_off, md) && offsets_ok(ch->up_off, mu) && offsets_ok(ch->orig_off, ch->m) &&
-             ids_ok(ch->perm, ch->n) && ids_ok(ch->down_src, ch->n) && ids_ok(ch->up_dst, ch->n) &&
+             ids_ok(ch->perm, ch->n) && ids_ok(ch->bfs, ch->n) && ids_ok(ch->down_src, ch->n) && ids_ok(ch->up_dst, ch->n) &&
              ids_ok(ch->orig_head, ch->n) && ch->level_off[0] == 0 && ch->level_off[ch->L] == ch->n;
         if (ok) {
             ch->pos.assign(n, -1);

@@ -18,6 +18,7 @@
 
 #include "ch_internal.h"
 #include "iso_device.cuh"
+#include "sweep_schedule.h"
 #include "../../include/iso.h"
 
 namespace {
@@ -113,6 +114,14 @@ struct iso_graph {
     int32_t* pos = nullptr;
     int32_t* level_off = nullptr;
     std::vector<int32_t> h_level_off;
+    // host copies for building sweep schedules
+    std::vector<uint32_t> h_down_off;
+    std::vector<int32_t> h_down_src, h_bfs;
+    struct CachedSchedule {
+        int vpb, narrow_width, delay;
+        std::shared_ptr<SweepSchedule> s;
+    };
+    std::vector<CachedSchedule> schedules;
     std::mutex mu;
     iso_workspace* query_ws[7] = {};
     std::vector<void*> owned;
@@ -145,9 +154,12 @@ struct iso_workspace {
     void* mask = nullptr;
     uint8_t* upflag = nullptr;
     int32_t* io = nullptr;       // src[K], tau[K]
-    int32_t* ctl = nullptr;      // status[4], bar[2], pad[2], ecnt[K], upcnt[K], level_done[L]
-    int32_t* chunk_off = nullptr;  // [L+1] TMA sweep: first chunk of every level block
-    int32_t* level_mode = nullptr; // [L] TMA sweep: 1 = a warp per vertex
+    int32_t* ctl = nullptr;      // status[4], bar[2], pad[2], ecnt[K], upcnt[K]
+    int4* sched_info = nullptr;    // [Q] TMA sweep schedule
+    int32_t* pred_off = nullptr;   // [Q+1]
+    int32_t* pred = nullptr;       // dependency positions
+    int32_t* done = nullptr;       // [Q] zeroed per batch
+    int Q = 0;
     unsigned long long* upmask = nullptr;  // [n] TMA sweep: lanes with upward labels
     int vpb = 0;
     int2* pairs = nullptr;
@@ -180,8 +192,7 @@ struct iso_workspace {
     uint32_t* bar() { return (uint32_t*)(ctl + 4); }
     int32_t* ecnt() { return ctl + 8; }
     int32_t* upcnt() { return ctl + 8 + K; }
-    uint32_t* level_done() { return (uint32_t*)(ctl + 8 + 2 * K); }
-    size_t ctl_words() const { return 8 + 2 * (size_t)K + (size_t)g->L; }
+    size_t ctl_words() const { return 8 + 2 * (size_t)K; }
 
     void* alloc(size_t bytes) {
         void* p = g->A.get(bytes, stream);
@@ -223,20 +234,37 @@ int build_schedule(iso_workspace* ws) {
     if (!ws->sched) { iso::set_error("workspace: device allocation failed"); return ISO_E_NOMEM; }
     ISO_CK(cudaMemcpyAsync(ws->sched, steps.data(), steps.size() * sizeof(int4), cudaMemcpyHostToDevice,
                            ws->stream));
-    // TMA sweep: levels narrower than one chunk per CTA get a warp per vertex
-    std::vector<int32_t> co((size_t)g->L + 1, 0), mode((size_t)g->L, 0);
-    const int narrow_chunk = 31;  // consumer warps per CTA
-    for (int j = 0; j < g->L; ++j) {
-        const int w = g->h_level_off[j + 1] - g->h_level_off[j];
-        mode[j] = ws->narrow_width > 0 && w < ws->narrow_width ? 1 : 0;
-        const int per = mode[j] ? narrow_chunk : ws->vpb;
-        co[j + 1] = co[j] + (w + per - 1) / per;
+    if (ws->kernel == 1) {
+        // TMA sweep: locality-ordered chunk schedule, cached on the graph
+        const int delay = 2 * ws->grid;
+        std::shared_ptr<SweepSchedule> sc;
+        for (auto& c : g->schedules)
+            if (c.vpb == ws->vpb && c.narrow_width == ws->narrow_width && c.delay == delay) sc = c.s;
+        if (!sc) {
+            sc = std::make_shared<SweepSchedule>();
+            if (iso_make_schedule(g->n, g->L, g->h_level_off.data(), g->h_down_off.data(), g->h_down_src.data(),
+                                  g->h_bfs.data(), ws->vpb, 31, ws->narrow_width, delay, sc.get()) != 0) {
+                iso::set_error("workspace: could not build the sweep schedule");
+                return ISO_E_INVAL;
+            }
+            g->schedules.push_back({ws->vpb, ws->narrow_width, delay, sc});
+        }
+        ws->Q = sc->Q;
+        ws->sched_info = (int4*)ws->alloc((size_t)sc->Q * sizeof(int4));
+        ws->pred_off = (int32_t*)ws->alloc(((size_t)sc->Q + 1) * 4);
+        ws->pred = (int32_t*)ws->alloc(std::max<size_t>(sc->pred.size(), 1) * 4);
+        ws->done = (int32_t*)ws->alloc((size_t)sc->Q * 4);
+        if (!ws->sched_info || !ws->pred_off || !ws->pred || !ws->done) {
+            iso::set_error("workspace: device allocation failed");
+            return ISO_E_NOMEM;
+        }
+        ISO_CK(cudaMemcpyAsync(ws->sched_info, sc->info.data(), (size_t)sc->Q * sizeof(int4), cudaMemcpyHostToDevice,
+                               ws->stream));
+        ISO_CK(cudaMemcpyAsync(ws->pred_off, sc->pred_off.data(), ((size_t)sc->Q + 1) * 4, cudaMemcpyHostToDevice,
+                               ws->stream));
+        if (!sc->pred.empty())
+            ISO_CK(cudaMemcpyAsync(ws->pred, sc->pred.data(), sc->pred.size() * 4, cudaMemcpyHostToDevice, ws->stream));
     }
-    ws->chunk_off = (int32_t*)ws->alloc(co.size() * 4);
-    ws->level_mode = (int32_t*)ws->alloc(mode.size() * 4);
-    if (!ws->chunk_off || !ws->level_mode) { iso::set_error("workspace: device allocation failed"); return ISO_E_NOMEM; }
-    ISO_CK(cudaMemcpyAsync(ws->chunk_off, co.data(), co.size() * 4, cudaMemcpyHostToDevice, ws->stream));
-    ISO_CK(cudaMemcpyAsync(ws->level_mode, mode.data(), mode.size() * 4, cudaMemcpyHostToDevice, ws->stream));
     ISO_CK(cudaStreamSynchronize(ws->stream));
     return ISO_OK;
 }
@@ -268,6 +296,8 @@ int enqueue(iso_workspace* ws, bool want_dist, bool capturing) {
     cudaStream_t s = ws->stream;
     const int K = ws->K;
     ISO_CK(cudaMemsetAsync(ws->ctl, 0, ws->ctl_words() * 4, s));
+    if (ws->done) ISO_CK(cudaMemsetAsync(ws->done, 0, (size_t)ws->Q * 4, s));
+    if (ws->trace) ISO_CK(cudaMemsetAsync(ws->trace, 0, ((size_t)g->L + 2) * 8, s));
     ISO_CK(record(ws->ev[0], s, capturing));
 
     UpParams up{};
@@ -287,9 +317,11 @@ int enqueue(iso_workspace* ws, bool want_dist, bool capturing) {
     sw.timeout_ns = ws->timeout_ns; sw.n = g->n; sw.L = g->L; sw.nsched = ws->nsched; sw.cap = ws->gcap;
     sw.last_level_block = g->L - 1; sw.write_all = want_dist ? 1 : 0; sw.bar_extra = ws->bar_extra;
     sw.trace = ws->trace;
-    sw.chunk_off = ws->chunk_off;
-    sw.level_mode = ws->level_mode;
-    sw.level_done = ws->level_done();
+    sw.sched_info = ws->sched_info;
+    sw.pred_off = ws->pred_off;
+    sw.pred = ws->pred;
+    sw.done = ws->done;
+    sw.Q = ws->Q;
     sw.upmask = ws->upmask;
     if (ws->kernel == 1) ISO_CK(iso_launch_sweep_tma(sw, K, ws->tpv, ws->grid, s));
     else ISO_CK(iso_launch_sweep(sw, K, ws->tpv, ws->grid, s));
@@ -401,6 +433,15 @@ extern "C" int iso_upload_graph(const iso_ch* ch, const iso_alloc* alloc, void* 
         free_all(); return rc;
     }
     ISO_CK(cudaStreamSynchronize(g->stream));
+    try {
+        g->h_down_off = off32;
+        g->h_down_src = ch->down_src;
+        g->h_bfs = ch->bfs;
+    } catch (const std::bad_alloc&) {
+        free_all();
+        iso::set_error("iso_upload_graph: out of host memory");
+        return ISO_E_NOMEM;
+    }
     for (size_t i = 0; i <= n; ++i) off32[i] = (uint32_t)ch->up_off[i];
     arcs.assign(ch->up_dst.size() + 2, make_int2(0, 0));
     for (size_t i = 0; i < ch->up_dst.size(); ++i) arcs[i] = make_int2(ch->up_dst[i], ch->up_w[i]);

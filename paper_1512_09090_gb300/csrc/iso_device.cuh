@@ -71,9 +71,12 @@ struct SweepParams {
     int write_all;             // store every d row (distances requested)
     int bar_extra;             // testing: extra arrivals a barrier waits for
     long long* trace;          // nullable: global ns; layout depends on the kernel (see iso_api.cu)
-    const int32_t* chunk_off;  // [L+1] first chunk of every level block (TMA kernel)
-    const int32_t* level_mode; // [L] 0: a thread group per vertex, 1: a warp per vertex (TMA kernel)
-    uint32_t* level_done;      // [L] chunks completed per level block (TMA kernel), zeroed per batch
+    // TMA kernel: chunk schedule (see schedule.cpp) and its progress
+    const int4* sched_info;    // [Q] {v0, v1, level block, mode} per schedule position
+    const int32_t* pred_off;   // [Q+1] positions each position depends on ...
+    const int32_t* pred;       // ... pred[pred_off[q] .. pred_off[q+1])
+    int32_t* done;             // [Q] 1 once a position is complete; zeroed per batch
+    int Q;
     unsigned long long* upmask;// [n] lanes with an upward label (TMA kernel)
 };
 

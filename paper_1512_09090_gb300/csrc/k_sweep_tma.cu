@@ -10,23 +10,23 @@
 // The upward search has already written each lane's labels into the rows
 // (upmask[v] says which lanes), so the walk starts at once.
 //
-// Work is cut into chunks of VPB consecutive vertices of one level; chunk q
-// (numbered across all levels in sweep order) belongs to CTA q mod G.  Each
-// CTA (1024 threads, one per SM) has 31 consumer warps and one producer warp.
+// Work is cut into chunks of VPB consecutive vertices of one level and run in
+// the order of a host-built schedule (schedule.cpp) that interleaves levels
+// region by region for L2 reuse; schedule position q belongs to CTA q mod G.
+// Each CTA (1024 threads, one per SM) has 31 consumer warps and one producer
+// warp.
 // The producer walks the CTA's chunks and copies each chunk's CSR offsets and
 // its contiguous block of incoming downward arcs into one of kStages shared-
 // memory buffers with cp.async.bulk, completing on the buffer's "full"
-// mbarrier; consumers release a buffer on its "empty" mbarrier, and the
-// producer then publishes the chunk as done (fence + atomicAdd on its level's
-// counter).  Levels are not separated by grid barriers: a warp waits, before
-// gathering rows for a chunk of level block j, until block j-1 is complete,
-// which implies every earlier block is.  The graph is read-only, so copies run
-// ahead of those waits; only the label rows d[u] are gathered after them, with
-// ld.global.cg.  Narrow levels use a warp per vertex: its groups of TPV
+// mbarrier; consumers release a buffer on its "empty" mbarrier, and the last
+// consumer warp to finish a chunk marks its position complete.  There are no
+// grid barriers: before copying chunk q the producer warp waits until every
+// position q depends on is complete, so the consumers of q only start after its
+// dependencies and gather the label rows d[u] with ld.global.cg.  Narrow levels use a warp per vertex: its groups of TPV
 // threads take every (32/TPV)-th arc, so a vertex with many arcs needs one
 // round of gathers, and chunks are 31 vertices so more CTAs share the level.
 //
-// Every wait (mbarrier, level counter) is bounded: past the limit
+// Every wait (mbarrier, dependency flags) is bounded: past the limit
 // the kernel records kStTimeout, stops issuing copies, waits (bounded) for the
 // copies it already issued, and returns.
 #include "iso_device.cuh"
@@ -50,6 +50,8 @@ struct Meta {
     int v0, v1;   // vertices [v0, v1)
     int abase;    // first arc index held in the stage buffer
     int flags;    // bit 0: arcs did not fit (read them from global memory); bit 1: warp per vertex
+    int q, level; // schedule position and level block
+    int pad[2];
 };
 
 struct Smem {
@@ -59,6 +61,7 @@ struct Smem {
     Meta meta[kStages];
     unsigned long long full[kStages];
     unsigned long long empty[kStages];
+    int finished[kStages];  // consumer warps done with the chunk in each stage
     int ok;
 };
 
@@ -149,25 +152,18 @@ __device__ __forceinline__ int lane_of(int sub, int i) {
     else return sub * LPT + i;
 }
 
-// The CTA's chunks: global chunk q (level blocks in sweep order, VPB vertices
-// per chunk, chunk_off[j] = first chunk of block j) belongs to CTA q mod G, and
-// every CTA takes its chunks in increasing q.  Both warp roles walk this order.
+// The CTA's chunks: schedule position q belongs to CTA q mod G, and every CTA
+// takes its positions in increasing order.  Both warp roles walk this order.
 struct ChunkWalk {
     const SweepParams& p;
-    int vpb, q, j;
-    __device__ ChunkWalk(const SweepParams& pp, int v) : p(pp), vpb(v), q(blockIdx.x), j(0) {}
-    // Next chunk of this CTA: vertices [v0, v1) of level block blk, processed
-    // with a thread group (mode 0) or a warp (mode 1) per vertex.  false at the end.
-    __device__ bool next(int& v0, int& v1, int& blk, int& mode) {
-        const int total = p.chunk_off[p.L];
-        if (q >= total) return false;
-        while (p.chunk_off[j + 1] <= q) ++j;
-        mode = p.level_mode[j];
-        const int per = mode ? kConsumers / 32 : vpb;
-        const int lo = p.level_off[j], hi = p.level_off[j + 1];
-        v0 = lo + (q - p.chunk_off[j]) * per;
-        v1 = min(v0 + per, hi);
-        blk = j;
+    int q;
+    __device__ explicit ChunkWalk(const SweepParams& pp) : p(pp), q(blockIdx.x) {}
+    // Next chunk: vertices [v0, v1) of level block blk at position pos, with a
+    // thread group (mode 0) or a warp (mode 1) per vertex.  false at the end.
+    __device__ bool next(int& v0, int& v1, int& blk, int& mode, int& pos) {
+        if (q >= p.Q) return false;
+        const int4 c = p.sched_info[q];
+        v0 = c.x; v1 = c.y; blk = c.z; mode = c.w; pos = q;
         q += gridDim.x;
         return true;
     }
@@ -179,25 +175,33 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* a) {
     return v;
 }
 
-// Bounded wait until all chunks of level block j are done (plus bar_extra
-// arrivals that never come when a test asks for a timeout).  false = gave up.
-__device__ bool wait_level(const SweepParams& p, int j) {
-    const uint32_t need = (uint32_t)(p.chunk_off[j + 1] - p.chunk_off[j]) + (uint32_t)p.bar_extra;
-    if (ld_acquire(p.level_done + j) >= need) return true;
+// Bounded wait, by a whole warp, until every position schedule position q
+// depends on is complete (plus bar_extra flags that never come when a test asks
+// for a timeout).  Returns false, the same on every lane, if it gave up.
+__device__ bool wait_deps(const SweepParams& p, int q, int lane) {
+    const int a = p.pred_off[q], b = p.pred_off[q + 1] + p.bar_extra;
     const unsigned long long t0 = global_ns();
-    uint32_t nap = 32;
-    for (uint32_t it = 1;; ++it) {
-        __nanosleep(nap);
-        if (nap < 256) nap <<= 1;
-        if (ld_acquire(p.level_done + j) >= need) return true;
-        if ((it & 15) == 0) {
-            if (*(volatile int32_t*)p.status != kStOk) return false;
-            if (global_ns() - t0 > (unsigned long long)p.timeout_ns || it > (1u << 26)) {
-                atomicCAS(p.status, kStOk, kStTimeout);
-                return false;
+    for (int base = a; base < b; base += 32) {
+        const int i = base + lane;
+        const bool real = i < p.pred_off[q + 1];
+        bool mine = i >= b || (real && ld_acquire(reinterpret_cast<const uint32_t*>(p.done + p.pred[i])) != 0u);
+        uint32_t nap = 32;
+        for (uint32_t it = 0; !__all_sync(0xffffffffu, mine); ++it) {
+            __nanosleep(nap);
+            if (nap < 256) nap <<= 1;
+            if (!mine && real) mine = ld_acquire(reinterpret_cast<const uint32_t*>(p.done + p.pred[i])) != 0u;
+            int give_up = 0;
+            if (lane == 0 && (it & 15) == 15) {
+                if (*(volatile int32_t*)p.status != kStOk) give_up = 1;
+                else if (global_ns() - t0 > (unsigned long long)p.timeout_ns || it > (1u << 26)) {
+                    atomicCAS(p.status, kStOk, kStTimeout);
+                    give_up = 1;
+                }
             }
+            if (__shfl_sync(0xffffffffu, give_up, 0)) return false;
         }
     }
+    return true;
 }
 
 // Gathers rows d[u] + len(u,v) for arcs a, a+STEP, a+2*STEP, ... < e into acc.
@@ -255,33 +259,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tma(SweepParams p) {
         for (int i = 0; i < kStages; ++i) {
             mbar_init(&sm.full[i], 1);
             mbar_init(&sm.empty[i], kConsumers / 32);
+            sm.finished[i] = 0;
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
 
     if (warp == kConsumers / 32) {
-        // ---------------- producer warp: lane 0 copies chunks and reports them done ----------------
-        if (lane == 0) {
-            ChunkWalk walk(p, VPB);
-            int blk_of[kStages] = {};
-            int it = 0;
-            bool ok = true;
-            // chunk i - kStages has been consumed: publish it to the other CTAs
-            auto publish = [&](int i) {
-                const int stage = i % kStages;
-                if (!mbar_wait(&sm.empty[stage], (uint32_t)(i / kStages) & 1u, p)) return false;
-                __threadfence();
-                const uint32_t jb = (uint32_t)blk_of[stage];
-                const uint32_t need = (uint32_t)(p.chunk_off[jb + 1] - p.chunk_off[jb]);
-                if (atomicAdd(p.level_done + jb, 1u) + 1u == need && p.trace)
-                    p.trace[1 + jb] = (long long)global_ns();
-                return true;
-            };
-            int v0, v1, blk, mode;
-            while (ok && walk.next(v0, v1, blk, mode)) {
-                const int stage = it % kStages;
-                if (it >= kStages && !publish(it - kStages)) { ok = false; break; }
+        // ---------------- producer warp: checks dependencies, copies chunks ----------------
+        ChunkWalk walk(p);
+        int it = 0;
+        int v0, v1, blk, mode, pos;
+        while (walk.next(v0, v1, blk, mode, pos)) {
+            const int stage = it % kStages;
+            const uint32_t round = (uint32_t)(it / kStages);
+            int fine = 1;
+            if (lane == 0) fine = mbar_wait(&sm.empty[stage], (round & 1u) ^ 1u, p);
+            fine = __shfl_sync(0xffffffffu, fine, 0);
+            if (fine) fine = wait_deps(p, pos, lane);
+            if (!fine) break;
+            if (lane == 0) {
                 const uint32_t off0 = __ldg(p.down_off + v0), off1 = __ldg(p.down_off + v1);
                 const int ob = v0 & ~3;
                 const uint32_t obytes = (uint32_t)(((v1 + 1 - ob) * 4 + 15) & ~15);
@@ -289,20 +286,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tma(SweepParams p) {
                 const uint32_t na = off1 - ab;
                 const bool big = na > (uint32_t)kArcCap;
                 const uint32_t abytes = big ? 0u : ((na * 8u + 15u) & ~15u);
-                sm.meta[stage] = Meta{v0, v1, (int)ab, (big ? 1 : 0) | (mode ? 2 : 0)};
-                blk_of[stage] = blk;
+                sm.meta[stage] = Meta{v0, v1, (int)ab, (big ? 1 : 0) | (mode ? 2 : 0), pos, blk, {0, 0}};
                 mbar_expect_tx(&sm.full[stage], obytes + abytes);
                 bulk_load(sm.offs[stage], p.down_off + ob, obytes, &sm.full[stage]);
                 if (abytes) bulk_load(sm.arcs[stage], p.down_arc + ab, abytes, &sm.full[stage]);
-                ++it;
             }
-            const int first = it > kStages ? it - kStages : 0;
-            for (int i = first; i < it; ++i) {
-                if (ok) ok = publish(i);
-                // every issued copy must land before the CTA exits
-                mbar_wait(&sm.full[i % kStages], (uint32_t)(i / kStages) & 1u, p);
-            }
+            __syncwarp();
+            ++it;
         }
+        // every issued copy must land before the CTA exits
+        if (lane == 0)
+            for (int i = it > kStages ? it - kStages : 0; i < it; ++i)
+                mbar_wait(&sm.full[i % kStages], (uint32_t)(i / kStages) & 1u, p);
         __syncthreads();
         return;
     }
@@ -316,30 +311,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tma(SweepParams p) {
         const int32_t t = p.tau[tid];
         sm.tau[tid] = t < 0 ? 0u : (uint32_t)t;
     }
-    if (tid == 0) sm.ok = 0;  // highest level block known complete, + 1
+    if (tid == 0) sm.ok = 0;  // positions below sm.ok are known complete
     asm volatile("bar.sync 1, 992;" ::: "memory");
     if (p.trace && tid == 0 && blockIdx.x == 0) p.trace[0] = p.trace[p.L + 1] = (long long)global_ns();
 
-    ChunkWalk walk(p, VPB);
+    ChunkWalk walk(p);
     bool alive = true;
-    int it = 0, ready_blk = 0;  // blocks < ready_blk are known complete
-    int v0, v1, j, mode;
-    while (walk.next(v0, v1, j, mode)) {
+    int it = 0;
+    int v0, v1, j, mode, pos;
+    while (walk.next(v0, v1, j, mode, pos)) {
         const int stage = it % kStages;
         const uint32_t round = (uint32_t)(it / kStages);
         ++it;
-        // predecessors live in blocks < j; block j-1 complete implies all of them are
-        if (alive && j > ready_blk) {
-            bool ok = true;
-            if (lane == 0 && *(volatile int*)&sm.ok < j) {
-                ok = wait_level(p, j - 1);
-                if (ok) atomicMax(&sm.ok, j);
-            }
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            __syncwarp();
-            if (ok) ready_blk = j;
-            else alive = false;
-        }
         const bool ready = __all_sync(0xffffffffu, alive && mbar_wait(&sm.full[stage], round & 1u, p));
         if (ready) {
             const Meta mt = sm.meta[stage];
@@ -402,7 +385,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tma(SweepParams p) {
             if (valid && sub == 0 && g == 0) static_cast<MaskT*>(p.mask)[v] = (MaskT)bits;
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(&sm.empty[stage]);
+        if (lane == 0) {
+            // the last warp to finish the chunk publishes it to the other CTAs
+            __threadfence_block();
+            if (atomicAdd(&sm.finished[stage], 1) == kConsumers / 32 - 1) {
+                __threadfence_block();
+                sm.finished[stage] = 0;
+                __threadfence();
+                *(volatile int32_t*)(p.done + pos) = 1;
+                if (p.trace) atomicMax((unsigned long long*)p.trace + 1 + j, global_ns());
+            }
+            mbar_arrive(&sm.empty[stage]);
+        }
     }
     __syncthreads();
 }

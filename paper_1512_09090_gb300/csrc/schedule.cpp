@@ -1,0 +1,118 @@
+// Chunk schedule of the TMA-staged sweep (host side).
+//
+// PHAST's scanning phase (Section 2) is correct in any order in which every
+// vertex comes after the sources of its downward arcs; the level order is one
+// such order.  The sweep cuts every level into chunks of consecutive vertices
+// and runs them in the order built here: a topological order of the chunk
+// dependency graph (chunk c depends on every chunk holding a source of a
+// downward arc into c) chosen by greedy list scheduling that prefers the chunk
+// with the smallest spatial key (the BFS rank of its first vertex in the input
+// graph).  Chunks of all levels of one region then run close together in time,
+// so a label row is still in L2 when the next levels read it, instead of being
+// fetched from HBM once per level as a level-by-level sweep must.  A chunk only
+// becomes eligible `delay` positions after its last dependency, so that the
+// device rarely has to wait for one.
+//
+// For position q the device receives {v0, v1, level block, mode} and the list
+// of positions q depends on; it starts chunk q once all of them are complete.
+#include <algorithm>
+#include <cstdint>
+#include <queue>
+#include <tuple>
+#include <vector>
+
+#include "sweep_schedule.h"
+
+int iso_make_schedule(int n, int L, const int32_t* level_off, const uint32_t* down_off, const int32_t* down_src,
+                      const int32_t* bfs, int vpb, int narrow_chunk, int narrow_width, int delay,
+                      SweepSchedule* out) {
+    if (n <= 0 || L <= 0 || vpb <= 0 || narrow_chunk <= 0) return -1;
+    // chunks in level order
+    std::vector<int32_t> cv0, cv1, clev, cmode;
+    std::vector<int32_t> chunk_of(n);
+    for (int j = 0; j < L; ++j) {
+        const int lo = level_off[j], hi = level_off[j + 1];
+        const int mode = narrow_width > 0 && hi - lo < narrow_width ? 1 : 0;
+        const int per = mode ? narrow_chunk : vpb;
+        for (int b = lo; b < hi; b += per) {
+            const int c = (int)cv0.size();
+            const int e = std::min(b + per, hi);
+            cv0.push_back(b); cv1.push_back(e); clev.push_back(j); cmode.push_back(mode);
+            for (int v = b; v < e; ++v) chunk_of[v] = c;
+        }
+    }
+    const int Q = (int)cv0.size();
+    // dependency edges pred -> c, each distinct pair once
+    std::vector<int32_t> mark(Q, -1), indeg(Q, 0), soff(Q + 1, 0);
+    for (int pass = 0; pass < 2; ++pass) {
+        std::fill(mark.begin(), mark.end(), -1);
+        std::vector<int32_t> fill;
+        if (pass == 1) {
+            for (int c = 0; c < Q; ++c) soff[c + 1] += soff[c];
+            fill.assign(soff.begin(), soff.end() - 1);
+            out->succ.assign(soff[Q], 0);
+        }
+        for (int c = 0; c < Q; ++c) {
+            for (int v = cv0[c]; v < cv1[c]; ++v)
+                for (uint32_t a = down_off[v]; a < down_off[v + 1]; ++a) {
+                    const int pc = chunk_of[down_src[a]];
+                    if (mark[pc] == c) continue;
+                    mark[pc] = c;
+                    if (pass == 0) { soff[pc + 1]++; indeg[c]++; }
+                    else out->succ[fill[pc]++] = c;
+                }
+        }
+    }
+    // greedy list scheduling: smallest spatial key among eligible chunks
+    using Item = std::pair<int64_t, int32_t>;  // (key, chunk)
+    std::priority_queue<Item, std::vector<Item>, std::greater<Item>> ready;
+    std::priority_queue<std::tuple<int64_t, int64_t, int32_t>, std::vector<std::tuple<int64_t, int64_t, int32_t>>,
+                        std::greater<std::tuple<int64_t, int64_t, int32_t>>>
+        waiting;  // (eligible position, key, chunk)
+    std::vector<int64_t> earliest(Q, 0);
+    std::vector<int32_t> pos_of(Q, -1);
+    // spatial key, then higher level first
+    auto key = [&](int c) { return (int64_t)bfs[cv0[c]] * (L + 1) + clev[c]; };
+    for (int c = 0; c < Q; ++c)
+        if (indeg[c] == 0) ready.push({key(c), c});
+    out->info.resize(Q);
+    for (int q = 0; q < Q; ++q) {
+        while (!waiting.empty() && std::get<0>(waiting.top()) <= q) {
+            ready.push({std::get<1>(waiting.top()), std::get<2>(waiting.top())});
+            waiting.pop();
+        }
+        if (ready.empty()) {  // nothing eligible yet: take the soonest one
+            if (waiting.empty()) return -1;  // cycle: cannot happen for a valid hierarchy
+            ready.push({std::get<1>(waiting.top()), std::get<2>(waiting.top())});
+            waiting.pop();
+        }
+        const int c = ready.top().second;
+        ready.pop();
+        pos_of[c] = q;
+        out->info[q] = {cv0[c], cv1[c], clev[c], cmode[c]};
+        for (int32_t i = soff[c]; i < soff[c + 1]; ++i) {
+            const int s = out->succ[i];
+            earliest[s] = std::max<int64_t>(earliest[s], (int64_t)q + delay);
+            if (--indeg[s] == 0) waiting.push({earliest[s], key(s), s});
+        }
+    }
+    // dependency lists by position
+    out->pred_off.assign(Q + 1, 0);
+    for (int c = 0; c < Q; ++c)
+        for (int32_t i = soff[c]; i < soff[c + 1]; ++i) out->pred_off[pos_of[out->succ[i]] + 1]++;
+    for (int q = 0; q < Q; ++q) out->pred_off[q + 1] += out->pred_off[q];
+    out->pred.assign(out->pred_off[Q], 0);
+    {
+        std::vector<int32_t> fill(out->pred_off.begin(), out->pred_off.end() - 1);
+        for (int c = 0; c < Q; ++c)
+            for (int32_t i = soff[c]; i < soff[c + 1]; ++i) {
+                const int qs = pos_of[out->succ[i]];
+                if (pos_of[c] >= qs) return -1;  // not topological: refuse
+                out->pred[fill[qs]++] = pos_of[c];
+            }
+    }
+    out->succ.clear();
+    out->succ.shrink_to_fit();
+    out->Q = Q;
+    return 0;
+}

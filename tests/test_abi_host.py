@@ -49,6 +49,10 @@ def check_structure(ch, n):
     assert np.all(level_of[A["up_dst"]] > level_of[tails])
     assert np.all(A["down_w"] >= 0) and np.all(A["up_w"] >= 0)
     assert np.array_equal(np.sort(A["orig_id"]), np.arange(st["m"]))
+    assert np.array_equal(np.sort(A["bfs"]), np.arange(n))
+    # within a level, sweep order follows the BFS rank
+    for j in range(L):
+        assert np.all(np.diff(A["bfs"][lo[j]:lo[j + 1]]) > 0)
     return A
 
 
