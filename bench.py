@@ -235,6 +235,7 @@ def main():
     ap.add_argument("--fuse", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--sweep-kernel", type=int, default=0)
+    ap.add_argument("--delay", type=int, default=0, help="schedule delay (TMA sweep)")
     ap.add_argument("--trace", action="store_true", help="print per-step sweep times to stderr")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -270,6 +271,8 @@ def main():
         opts["ctas_per_sm"] = args.ctas_per_sm
     if args.sweep_kernel:
         opts["sweep_kernel"] = args.sweep_kernel
+    if args.delay:
+        opts["schedule_delay"] = args.delay
     if args.trace:
         opts["record_trace"] = 1
     ws = P.Workspace(dg, k, **opts)

@@ -148,7 +148,9 @@ typedef struct {
                                    arrivals that never come, so every wait times out */
     int32_t sweep_kernel;       /* 0 = auto (TMA-staged arc blocks), 1 = TMA-staged, 2 = plain loads */
     int32_t record_trace;       /* 1 = record the device time of every sweep step (iso_workspace_trace) */
-    int32_t reserved[5];        /* must be zero */
+    int32_t schedule_delay;     /* TMA-staged sweep: a chunk is scheduled at least this many positions
+                                   after the chunks it depends on; 0 = auto (twice the CTA count) */
+    int32_t reserved[4];        /* must be zero */
 } iso_query_opts;
 
 /* Answer k isochrone queries (source sources[i], limit taus[i]) in sweeps of

@@ -141,6 +141,7 @@ struct iso_workspace {
     int K = 0, tpv = 0, grid = 0, fuse_width = 0;
     int kernel = 1;              // 1 = TMA-staged sweep, 2 = plain loads
     int narrow_width = 0;        // TMA sweep: levels narrower than this use a warp per vertex
+    int sched_delay = 0;         // TMA sweep: schedule distance to dependencies
     bool record_trace = false;
     long long* trace = nullptr;  // device [nsched + 1]
     std::vector<long long> h_trace;
@@ -236,7 +237,7 @@ int build_schedule(iso_workspace* ws) {
                            ws->stream));
     if (ws->kernel == 1) {
         // TMA sweep: locality-ordered chunk schedule, cached on the graph
-        const int delay = 2 * ws->grid;
+        const int delay = ws->sched_delay;
         std::shared_ptr<SweepSchedule> sc;
         for (auto& c : g->schedules)
             if (c.vpb == ws->vpb && c.narrow_width == ws->narrow_width && c.delay == delay) sc = c.s;
@@ -390,7 +391,7 @@ int check_opts(const iso_query_opts* o) {
     for (int r : o->reserved)
         if (r) { iso::set_error("iso_query_opts: reserved fields must be zero"); return ISO_E_INVAL; }
     if (o->threads_per_vertex < 0 || o->ctas_per_sm < 0 || o->fuse_width < -1 || o->barrier_timeout_ns < 0 ||
-        o->debug_barrier_extra < 0) {
+        o->debug_barrier_extra < 0 || o->schedule_delay < 0) {
         iso::set_error("iso_query_opts: negative field");
         return ISO_E_INVAL;
     }
@@ -499,6 +500,7 @@ extern "C" int iso_workspace_create(iso_graph* g, int32_t lanes, const iso_query
     // a level narrower than one chunk of ws->vpb vertices per CTA runs with a warp per vertex
     ws->narrow_width = o.fuse_width < 0 ? 0 : (o.fuse_width > 0 ? o.fuse_width : ws->grid * vpb);
     ws->record_trace = o.record_trace != 0 && ws->kernel == 1;
+    ws->sched_delay = o.schedule_delay > 0 ? o.schedule_delay : 2 * ws->grid;
     ws->use_graph = opts ? opts->use_cuda_graph != 0 : false;
     if (opts && opts->barrier_timeout_ns) ws->timeout_ns = opts->barrier_timeout_ns;
     ws->bar_extra = opts ? opts->debug_barrier_extra : 0;
@@ -715,7 +717,8 @@ bool same_config(const iso_workspace* ws, const iso_query_opts& o) {
     const long long timeout = o.barrier_timeout_ns ? o.barrier_timeout_ns : 2000000000LL;
     return ws->kernel == kernel && ws->tpv == tpv && ws->grid == ws->g->num_sms * per_sm &&
            ws->fuse_width == fuse && ws->use_graph == (o.use_cuda_graph != 0) && ws->timeout_ns == timeout &&
-           ws->bar_extra == o.debug_barrier_extra && ws->record_trace == (o.record_trace != 0);
+           ws->bar_extra == o.debug_barrier_extra && ws->record_trace == (o.record_trace != 0 && kernel == 1) &&
+           ws->sched_delay == (o.schedule_delay > 0 ? o.schedule_delay : 2 * ws->g->num_sms * per_sm);
 }
 }  // namespace
 

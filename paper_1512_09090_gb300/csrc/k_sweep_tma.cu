@@ -20,9 +20,10 @@
 // memory buffers with cp.async.bulk, completing on the buffer's "full"
 // mbarrier; consumers release a buffer on its "empty" mbarrier, and the last
 // consumer warp to finish a chunk marks its position complete.  There are no
-// grid barriers: before copying chunk q the producer warp waits until every
-// position q depends on is complete, so the consumers of q only start after its
-// dependencies and gather the label rows d[u] with ld.global.cg.  Narrow levels use a warp per vertex: its groups of TPV
+// grid barriers: after starting the copy of chunk q (read-only graph data) the
+// producer warp waits until every position q depends on is complete and posts
+// that in shared memory; only then do the consumers gather the label rows d[u]
+// of q, with ld.global.cg.  Narrow levels use a warp per vertex: its groups of TPV
 // threads take every (32/TPV)-th arc, so a vertex with many arcs needs one
 // round of gathers, and chunks are 31 vertices so more CTAs share the level.
 //
@@ -62,6 +63,7 @@ struct Smem {
     unsigned long long full[kStages];
     unsigned long long empty[kStages];
     int finished[kStages];  // consumer warps done with the chunk in each stage
+    int ready_it[kStages];  // chunk (CTA-local index + 1) whose dependencies were seen complete
     int ok;
 };
 
@@ -179,17 +181,26 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t* a) {
 // depends on is complete (plus bar_extra flags that never come when a test asks
 // for a timeout).  Returns false, the same on every lane, if it gave up.
 __device__ bool wait_deps(const SweepParams& p, int q, int lane) {
-    const int a = p.pred_off[q], b = p.pred_off[q + 1] + p.bar_extra;
+    const int a = p.pred_off[q], b_real = p.pred_off[q + 1], b = b_real + p.bar_extra;
     const unsigned long long t0 = global_ns();
-    for (int base = a; base < b; base += 32) {
-        const int i = base + lane;
-        const bool real = i < p.pred_off[q + 1];
-        bool mine = i >= b || (real && ld_acquire(reinterpret_cast<const uint32_t*>(p.done + p.pred[i])) != 0u);
+    for (int base = a; base < b; base += 128) {
+        // up to four flags per lane, all loads in flight at once
+        bool mine[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int i = base + lane + 32 * t;
+            mine[t] = i >= b || (i < b_real && ld_acquire(reinterpret_cast<const uint32_t*>(p.done + p.pred[i])) != 0u);
+        }
         uint32_t nap = 32;
-        for (uint32_t it = 0; !__all_sync(0xffffffffu, mine); ++it) {
+        for (uint32_t it = 0; !__all_sync(0xffffffffu, mine[0] && mine[1] && mine[2] && mine[3]); ++it) {
             __nanosleep(nap);
             if (nap < 256) nap <<= 1;
-            if (!mine && real) mine = ld_acquire(reinterpret_cast<const uint32_t*>(p.done + p.pred[i])) != 0u;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int i = base + lane + 32 * t;
+                if (!mine[t] && i < b_real)
+                    mine[t] = ld_acquire(reinterpret_cast<const uint32_t*>(p.done + p.pred[i])) != 0u;
+            }
             int give_up = 0;
             if (lane == 0 && (it & 15) == 15) {
                 if (*(volatile int32_t*)p.status != kStOk) give_up = 1;
@@ -260,6 +271,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tma(SweepParams p) {
             mbar_init(&sm.full[i], 1);
             mbar_init(&sm.empty[i], kConsumers / 32);
             sm.finished[i] = 0;
+            sm.ready_it[i] = 0;
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -276,7 +288,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tma(SweepParams p) {
             int fine = 1;
             if (lane == 0) fine = mbar_wait(&sm.empty[stage], (round & 1u) ^ 1u, p);
             fine = __shfl_sync(0xffffffffu, fine, 0);
-            if (fine) fine = wait_deps(p, pos, lane);
             if (!fine) break;
             if (lane == 0) {
                 const uint32_t off0 = __ldg(p.down_off + v0), off1 = __ldg(p.down_off + v1);
@@ -293,6 +304,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tma(SweepParams p) {
             }
             __syncwarp();
             ++it;
+            // the copy is in flight; meanwhile wait for the chunk's dependencies
+            // and tell the consumers when its rows may be gathered
+            if (!wait_deps(p, pos, lane)) break;
+            __threadfence_block();
+            if (lane == 0) *(volatile int*)&sm.ready_it[stage] = it;
         }
         // every issued copy must land before the CTA exits
         if (lane == 0)
@@ -323,6 +339,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tma(SweepParams p) {
         const int stage = it % kStages;
         const uint32_t round = (uint32_t)(it / kStages);
         ++it;
+        // the producer posts ready_it once every position the chunk depends on is
+        // complete; only then may its rows be gathered
+        if (alive && lane == 0) {
+            const unsigned long long t0 = global_ns();
+            for (uint32_t n = 0; *(volatile int*)&sm.ready_it[stage] != it; ++n) {
+                __nanosleep(32);
+                if ((n & 255) == 255 && (*(volatile int32_t*)p.status != kStOk ||
+                                         global_ns() - t0 > (unsigned long long)p.timeout_ns)) {
+                    atomicCAS(p.status, kStOk, kStTimeout);
+                    alive = false;
+                    break;
+                }
+            }
+        }
+        alive = __shfl_sync(0xffffffffu, alive, 0);
+        __threadfence_block();
         const bool ready = __all_sync(0xffffffffu, alive && mbar_wait(&sm.full[stage], round & 1u, p));
         if (ready) {
             const Meta mt = sm.meta[stage];

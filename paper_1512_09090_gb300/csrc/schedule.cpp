@@ -96,20 +96,33 @@ int iso_make_schedule(int n, int L, const int32_t* level_off, const uint32_t* do
             if (--indeg[s] == 0) waiting.push({earliest[s], key(s), s});
         }
     }
-    // dependency lists by position
-    out->pred_off.assign(Q + 1, 0);
+    // Dependency lists by position, without the dependencies another
+    // dependency already implies: if c depends on p and on p', and p' depends
+    // on p, then p' completing implies p did (p' only started after p), so
+    // only p' is checked.  (One hop of the transitive reduction.)
+    std::vector<std::vector<int32_t>> preds(Q);
     for (int c = 0; c < Q; ++c)
-        for (int32_t i = soff[c]; i < soff[c + 1]; ++i) out->pred_off[pos_of[out->succ[i]] + 1]++;
+        for (int32_t i = soff[c]; i < soff[c + 1]; ++i) preds[out->succ[i]].push_back(c);
+    std::vector<int32_t> keep_mark(Q, -1), implied(Q, -1);
+    std::vector<std::vector<int32_t>> kept(Q);
+    for (int c = 0; c < Q; ++c) {
+        for (int32_t p : preds[c]) keep_mark[p] = c;
+        for (int32_t p1 : preds[c])
+            for (int32_t p2 : preds[p1])
+                if (keep_mark[p2] == c) implied[p2] = c;
+        for (int32_t p : preds[c])
+            if (implied[p] != c) kept[c].push_back(p);
+    }
+    out->pred_off.assign(Q + 1, 0);
+    for (int c = 0; c < Q; ++c) out->pred_off[pos_of[c] + 1] = (int32_t)kept[c].size();
     for (int q = 0; q < Q; ++q) out->pred_off[q + 1] += out->pred_off[q];
     out->pred.assign(out->pred_off[Q], 0);
-    {
-        std::vector<int32_t> fill(out->pred_off.begin(), out->pred_off.end() - 1);
-        for (int c = 0; c < Q; ++c)
-            for (int32_t i = soff[c]; i < soff[c + 1]; ++i) {
-                const int qs = pos_of[out->succ[i]];
-                if (pos_of[c] >= qs) return -1;  // not topological: refuse
-                out->pred[fill[qs]++] = pos_of[c];
-            }
+    for (int c = 0; c < Q; ++c) {
+        int32_t o = out->pred_off[pos_of[c]];
+        for (int32_t p : kept[c]) {
+            if (pos_of[p] >= pos_of[c]) return -1;  // not topological: refuse
+            out->pred[o++] = pos_of[p];
+        }
     }
     out->succ.clear();
     out->succ.shrink_to_fit();
