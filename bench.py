@@ -16,7 +16,6 @@ own batches; value = queries answered by all ranks / slowest rank's time.
 from __future__ import annotations
 
 import argparse
-import hashlib
 import json
 import os
 import statistics
@@ -63,33 +62,8 @@ def draw_taus(spec, k, seed):
 
 def load_graph_and_ch(name):
     """Generate the graph and build (or load a cached) contraction hierarchy."""
-    import paper_1512_09090_gb300 as P
-    from paper_1512_09090_gb300 import synth
-    t0 = time.time()
-    g = synth.workload_graph(name)
-    log(f"[bench] graph {name}: n={g.n} m={g.m} ({time.time() - t0:.1f}s)")
-    h = hashlib.sha1(json.dumps(synth.WORKLOADS[name], sort_keys=True).encode())
-    with open(os.path.join(ROOT, "paper_1512_09090_gb300", "csrc", "ch.cpp"), "rb") as f:
-        h.update(f.read())
-    path = os.path.join(CACHE, f"{name}-{h.hexdigest()[:12]}.ch")
-    if os.path.exists(path):
-        try:
-            ch = P.iso_load_ch(path)
-            log(f"[bench] CH loaded from cache {os.path.basename(path)}")
-            return g, ch
-        except Exception as e:  # rebuild below
-            log(f"[bench] cache unreadable ({e}); rebuilding")
-    t0 = time.time()
-    ch = P.iso_build_ch(g.n, g.tail, g.head, g.weight)
-    log(f"[bench] CH built in {time.time() - t0:.1f}s: {ch.stats()}")
-    try:
-        os.makedirs(CACHE, exist_ok=True)
-        tmp = path + f".tmp{os.getpid()}"
-        ch.save(tmp)
-        os.replace(tmp, path)
-    except OSError as e:
-        log(f"[bench] could not cache the CH: {e}")
-    return g, ch
+    from paper_1512_09090_gb300 import chcache
+    return chcache.workload_graph_and_ch(name, log=log)
 
 
 def sweep_bytes(A, k, write_all=False):
@@ -237,6 +211,9 @@ def main():
     ap.add_argument("--sweep-kernel", type=int, default=0)
     ap.add_argument("--delay", type=int, default=0, help="schedule delay (TMA sweep)")
     ap.add_argument("--trace", action="store_true", help="print per-step sweep times to stderr")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -263,18 +240,16 @@ def main():
     dg = P.iso_upload_graph(ch)
     k = spec["k"]
     opts = dict(use_cuda_graph=1)
-    if args.tpv:
-        opts["threads_per_vertex"] = args.tpv
-    if args.fuse:
-        opts["fuse_width"] = args.fuse
-    if args.ctas_per_sm:
-        opts["ctas_per_sm"] = args.ctas_per_sm
-    if args.sweep_kernel:
-        opts["sweep_kernel"] = args.sweep_kernel
-    if args.delay:
-        opts["schedule_delay"] = args.delay
-    if args.trace:
-        opts["record_trace"] = 1
+    tuned = None
+    if not args.no_autotune and not (args.tpv or args.delay or args.sweep_kernel):
+        from paper_1512_09090_gb300 import autotune
+        ts = synth.draw_sources(g, 4 * k, 777)
+        tt = draw_taus(spec["tau"], 4 * k, 778)
+        tuned = autotune.tune(dg, ts, tt, lanes_choices=(k,), reps=4, budget_s=90.0,
+                              cache_path=os.path.join(CACHE, "autotune.json"), log=log)
+        for key in ("threads_per_vertex", "schedule_delay"):
+            if key in tuned:
+                opts[key] = tuned[key]
     ws = P.Workspace(dg, k, **opts)
     nb = 16
     batches = []
@@ -358,6 +333,22 @@ def main():
         e2e = {"value": world * k * args.steps / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": 2 * 4 * k,
                "d2h_bytes_per_step": d2h // args.steps}
 
+    serving_stats = None
+    if not args.no_serving:
+        from paper_1512_09090_gb300 import serving
+        nreq = args.serve_requests
+        rate = 0.8 * (k * args.steps / (el_ms / 1e3))       # 80% of the measured batched capacity
+        s_src = synth.draw_sources(g, nreq, 4000 + rank)
+        s_tau = synth.draw_taus_loguniform(nreq, 600, 72000, 5000 + rank)
+        s_arr = synth.poisson_arrivals(nreq, rate, 6000 + rank)
+        sopts = {kk: v for kk, v in opts.items() if kk != "record_trace"}
+        with serving.IsoServer(dg, lanes=k, memory_fraction=0.5, max_workspaces=3, **sopts) as srv:
+            serving.run_poisson(srv, s_src[:64], s_tau[:64], s_arr[:64] - s_arr[0])   # warm-up
+            res, wall = serving.run_poisson(srv, s_src, s_tau, s_arr)
+            nws = len(srv.workspaces)
+        serving_stats = {"requests": nreq, "offered_qps": round(rate, 1), "achieved_qps": round(nreq / wall, 1),
+                         "workspaces": nws, "tau": "log-uniform [600, 72000]", "arrivals": "Poisson",
+                         **serving.latency_summary(res)}
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -383,6 +374,8 @@ def main():
             "latency_ms": {"p50": round(lat[len(lat) // 2], 3), "p99": round(lat[min(len(lat) - 1,
                                                                                      int(0.99 * len(lat)))], 3)},
             "phases_ms": {key: round(statistics.mean(p[key] for p in phases), 4) for key in phases[0]},
+            "serving": serving_stats,
+            "autotune": None if tuned is None else {kk: v for kk, v in tuned.items() if kk != "tried"},
             "gpu_launches": 4 * args.steps, "e2e": e2e}
     clocks = clk.summary()
     if clocks:

@@ -1,0 +1,102 @@
+"""Autotuner for batched isochrone queries.
+
+For a device graph it times one batch per candidate configuration -- lanes per
+sweep (k), threads per vertex, the narrow-level threshold and the schedule
+delay of the TMA-staged sweep -- and keeps the one with the highest query
+throughput.  Results are cached in a JSON file keyed by the graph's shape, so
+a process that uploads the same graph again skips the search.
+
+Every candidate runs the real query path on real inputs; the tuner only
+chooses among configurations whose results are identical by construction
+(each configuration computes the same labels).
+"""
+
+from __future__ import annotations
+
+import json
+import os
+import time
+
+import numpy as np
+
+from . import _lib
+
+# threads per vertex supported by the TMA-staged sweep, per lane class
+TPV_CHOICES = {1: (1,), 4: (1,), 8: (1,), 16: (2, 4), 32: (4, 8), 64: (8,)}
+
+
+def graph_key(g: _lib.DeviceGraph) -> str:
+    import torch
+    dev = torch.cuda.get_device_name(g.device)
+    return f"n{g.n}-m{g.m}-down{g.m_down}-L{g.levels}-{dev}"
+
+
+def _time_config(g, lanes, sources, taus, opts, reps):
+    import torch
+    ws = _lib.Workspace(g, lanes, use_cuda_graph=1, **opts)
+    try:
+        ws.submit(sources[:lanes], taus[:lanes])
+        ws.collect()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for r in range(reps):
+            s = sources[(r * lanes) % len(sources):][:lanes]
+            t = taus[(r * lanes) % len(taus):][:lanes]
+            if len(s) < lanes:
+                s, t = sources[:lanes], taus[:lanes]
+            ws.submit(s, t)
+            ws.collect()
+        el = time.perf_counter() - t0
+    finally:
+        ws.free()
+    return lanes * reps / el
+
+
+def tune(g: _lib.DeviceGraph, sources: np.ndarray, taus: np.ndarray, lanes_choices=(64,), reps: int = 5,
+         cache_path: str | None = None, budget_s: float = 120.0, log=None) -> dict:
+    """Best {"lanes", **iso_query_opts} for g on this kind of query mix."""
+    key = graph_key(g)
+    cache = {}
+    if cache_path and os.path.exists(cache_path):
+        try:
+            with open(cache_path) as f:
+                cache = json.load(f)
+        except (OSError, ValueError):
+            cache = {}
+    ck = f"{key}-lanes{'_'.join(map(str, lanes_choices))}"
+    if ck in cache:
+        return cache[ck]
+    import torch
+    sms = torch.cuda.get_device_properties(g.device).multi_processor_count
+    cands = []
+    for lanes in lanes_choices:
+        for tpv in TPV_CHOICES.get(lanes, (1,)):
+            for rounds in (4, 16):  # schedule delay in rounds of one chunk per CTA
+                cands.append({"lanes": lanes, "threads_per_vertex": tpv, "schedule_delay": rounds * sms})
+    start = time.perf_counter()
+    best, best_qps, tried = None, -1.0, []
+    for c in cands:
+        if time.perf_counter() - start > budget_s:
+            break
+        opts = {k: v for k, v in c.items() if k != "lanes"}
+        try:
+            qps = _time_config(g, c["lanes"], sources, taus, opts, reps)
+        except _lib.IsoError:
+            continue
+        tried.append({**c, "qps": round(qps, 1)})
+        if log:
+            log(f"[autotune] {c} -> {qps:.0f} q/s")
+        if qps > best_qps:
+            best, best_qps = c, qps
+    result = dict(best or {"lanes": lanes_choices[0]})
+    result["qps"] = round(best_qps, 1)
+    result["tried"] = tried
+    if cache_path:
+        cache[ck] = result
+        try:
+            os.makedirs(os.path.dirname(cache_path), exist_ok=True)
+            with open(cache_path, "w") as f:
+                json.dump(cache, f, indent=1)
+        except OSError:
+            pass
+    return result
