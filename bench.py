@@ -20,6 +20,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -67,7 +68,10 @@ def load_graph_and_ch(name):
 
 
 def sweep_bytes(A, k, write_all=False):
-    """Algorithmic bytes one sweep of k lanes must move."""
+    """Algorithmic bytes one sweep of k lanes must move: the CSR offsets and
+    every downward arc once, every stored label row written once, every row
+    that is the source of a downward arc read once, the in-range masks written,
+    the upward-label flags read and the level table."""
     n = A["perm"].shape[0]
     lo = A["level_off"]
     n_low = int(lo[-1] - lo[-2])                 # lowest level: rows not stored
@@ -85,7 +89,7 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"iso_bench_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
@@ -201,7 +205,7 @@ def run_reference(args, spec):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="grid18m_k64", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -210,6 +214,7 @@ def main():
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--sweep-kernel", type=int, default=0)
     ap.add_argument("--delay", type=int, default=0, help="schedule delay (TMA sweep)")
+    ap.add_argument("--solo", type=int, default=0, help="top-block level size limit (TMA sweep; -1 = none)")
     ap.add_argument("--trace", action="store_true", help="print per-step sweep times to stderr")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
@@ -250,6 +255,13 @@ def main():
         for key in ("threads_per_vertex", "schedule_delay"):
             if key in tuned:
                 opts[key] = tuned[key]
+    for flag, key in ((args.tpv, "threads_per_vertex"), (args.delay, "schedule_delay"),
+                      (args.sweep_kernel, "sweep_kernel"), (args.fuse, "fuse_width"),
+                      (args.ctas_per_sm, "ctas_per_sm"), (args.solo, "solo_width")):
+        if flag:
+            opts[key] = flag
+    if args.trace:
+        opts["record_trace"] = 1
     ws = P.Workspace(dg, k, **opts)
     nb = 16
     batches = []

@@ -68,6 +68,9 @@ bool is_device_ptr(const void* p) {
 }
 
 constexpr int kMaxLanes = 64;
+// default size limit of the levels in the top block of the TMA sweep (four
+// vertices per consumer warp)
+constexpr int kSoloWidth = 124;
 
 int lanes_class(int k) {
     if (k <= 1) return 1;
@@ -118,7 +121,7 @@ struct iso_graph {
     std::vector<uint32_t> h_down_off;
     std::vector<int32_t> h_down_src, h_bfs;
     struct CachedSchedule {
-        int vpb, narrow_width, delay;
+        int vpb, narrow_width, solo_levels, delay;
         std::shared_ptr<SweepSchedule> s;
     };
     std::vector<CachedSchedule> schedules;
@@ -142,6 +145,8 @@ struct iso_workspace {
     int kernel = 1;              // 1 = TMA-staged sweep, 2 = plain loads
     int narrow_width = 0;        // TMA sweep: levels narrower than this use a warp per vertex
     int sched_delay = 0;         // TMA sweep: schedule distance to dependencies
+    int solo_width = 0;          // TMA sweep: top levels up to this size run in one CTA (0: none)
+    int solo_levels = 0;         // ... how many levels that is on this graph
     bool record_trace = false;
     long long* trace = nullptr;  // device [nsched + 1]
     std::vector<long long> h_trace;
@@ -156,9 +161,8 @@ struct iso_workspace {
     uint8_t* upflag = nullptr;
     int32_t* io = nullptr;       // src[K], tau[K]
     int32_t* ctl = nullptr;      // status[4], bar[2], pad[2], ecnt[K], upcnt[K]
-    int4* sched_info = nullptr;    // [Q] TMA sweep schedule
-    int32_t* pred_off = nullptr;   // [Q+1]
-    int32_t* pred = nullptr;       // dependency positions
+    int4* sched_info = nullptr;    // [2Q] TMA sweep schedule: one SchedChunk per position
+    int32_t* pred = nullptr;       // dependency lists (padded, see sweep_schedule.h)
     int32_t* done = nullptr;       // [Q] zeroed per batch
     int Q = 0;
     unsigned long long* upmask = nullptr;  // [n] TMA sweep: lanes with upward labels
@@ -238,33 +242,42 @@ int build_schedule(iso_workspace* ws) {
     if (ws->kernel == 1) {
         // TMA sweep: locality-ordered chunk schedule, cached on the graph
         const int delay = ws->sched_delay;
+        // the top levels with at most solo_width vertices each form the top block
+        int solo = 0;
+        while (ws->solo_width > 0 && solo < g->L &&
+               g->h_level_off[solo + 1] - g->h_level_off[solo] <= ws->solo_width)
+            ++solo;
+        ws->solo_levels = solo;
+        static_assert(sizeof(SchedChunk) == 2 * sizeof(int4), "schedule record layout");
         std::shared_ptr<SweepSchedule> sc;
         for (auto& c : g->schedules)
-            if (c.vpb == ws->vpb && c.narrow_width == ws->narrow_width && c.delay == delay) sc = c.s;
+            if (c.vpb == ws->vpb && c.narrow_width == ws->narrow_width && c.solo_levels == solo && c.delay == delay)
+                sc = c.s;
         if (!sc) {
             sc = std::make_shared<SweepSchedule>();
             if (iso_make_schedule(g->n, g->L, g->h_level_off.data(), g->h_down_off.data(), g->h_down_src.data(),
-                                  g->h_bfs.data(), ws->vpb, 31, ws->narrow_width, delay, sc.get()) != 0) {
+                                  g->h_bfs.data(), ws->vpb, 31, ws->narrow_width, solo, delay, sc.get()) != 0) {
                 iso::set_error("workspace: could not build the sweep schedule");
                 return ISO_E_INVAL;
             }
-            g->schedules.push_back({ws->vpb, ws->narrow_width, delay, sc});
+            for (int q = 1; q < sc->Q; ++q)
+                if (sc->info[q].mode == 2) {  // the sweep runs the top block only as CTA 0's first chunk
+                    iso::set_error("workspace: top block not first in the sweep schedule");
+                    return ISO_E_INVAL;
+                }
+            g->schedules.push_back({ws->vpb, ws->narrow_width, solo, delay, sc});
         }
         ws->Q = sc->Q;
-        ws->sched_info = (int4*)ws->alloc((size_t)sc->Q * sizeof(int4));
-        ws->pred_off = (int32_t*)ws->alloc(((size_t)sc->Q + 1) * 4);
-        ws->pred = (int32_t*)ws->alloc(std::max<size_t>(sc->pred.size(), 1) * 4);
+        ws->sched_info = (int4*)ws->alloc((size_t)sc->Q * sizeof(SchedChunk));
+        ws->pred = (int32_t*)ws->alloc(sc->pred.size() * 4);
         ws->done = (int32_t*)ws->alloc((size_t)sc->Q * 4);
-        if (!ws->sched_info || !ws->pred_off || !ws->pred || !ws->done) {
+        if (!ws->sched_info || !ws->pred || !ws->done) {
             iso::set_error("workspace: device allocation failed");
             return ISO_E_NOMEM;
         }
-        ISO_CK(cudaMemcpyAsync(ws->sched_info, sc->info.data(), (size_t)sc->Q * sizeof(int4), cudaMemcpyHostToDevice,
-                               ws->stream));
-        ISO_CK(cudaMemcpyAsync(ws->pred_off, sc->pred_off.data(), ((size_t)sc->Q + 1) * 4, cudaMemcpyHostToDevice,
-                               ws->stream));
-        if (!sc->pred.empty())
-            ISO_CK(cudaMemcpyAsync(ws->pred, sc->pred.data(), sc->pred.size() * 4, cudaMemcpyHostToDevice, ws->stream));
+        ISO_CK(cudaMemcpyAsync(ws->sched_info, sc->info.data(), (size_t)sc->Q * sizeof(SchedChunk),
+                               cudaMemcpyHostToDevice, ws->stream));
+        ISO_CK(cudaMemcpyAsync(ws->pred, sc->pred.data(), sc->pred.size() * 4, cudaMemcpyHostToDevice, ws->stream));
     }
     ISO_CK(cudaStreamSynchronize(ws->stream));
     return ISO_OK;
@@ -319,7 +332,6 @@ int enqueue(iso_workspace* ws, bool want_dist, bool capturing) {
     sw.last_level_block = g->L - 1; sw.write_all = want_dist ? 1 : 0; sw.bar_extra = ws->bar_extra;
     sw.trace = ws->trace;
     sw.sched_info = ws->sched_info;
-    sw.pred_off = ws->pred_off;
     sw.pred = ws->pred;
     sw.done = ws->done;
     sw.Q = ws->Q;
@@ -391,7 +403,7 @@ int check_opts(const iso_query_opts* o) {
     for (int r : o->reserved)
         if (r) { iso::set_error("iso_query_opts: reserved fields must be zero"); return ISO_E_INVAL; }
     if (o->threads_per_vertex < 0 || o->ctas_per_sm < 0 || o->fuse_width < -1 || o->barrier_timeout_ns < 0 ||
-        o->debug_barrier_extra < 0 || o->schedule_delay < 0) {
+        o->debug_barrier_extra < 0 || o->schedule_delay < 0 || o->solo_width < -1) {
         iso::set_error("iso_query_opts: negative field");
         return ISO_E_INVAL;
     }
@@ -501,6 +513,7 @@ extern "C" int iso_workspace_create(iso_graph* g, int32_t lanes, const iso_query
     ws->narrow_width = o.fuse_width < 0 ? 0 : (o.fuse_width > 0 ? o.fuse_width : ws->grid * vpb);
     ws->record_trace = o.record_trace != 0 && ws->kernel == 1;
     ws->sched_delay = o.schedule_delay > 0 ? o.schedule_delay : 2 * ws->grid;
+    ws->solo_width = o.solo_width < 0 ? 0 : (o.solo_width > 0 ? o.solo_width : kSoloWidth);
     ws->use_graph = opts ? opts->use_cuda_graph != 0 : false;
     if (opts && opts->barrier_timeout_ns) ws->timeout_ns = opts->barrier_timeout_ns;
     ws->bar_extra = opts ? opts->debug_barrier_extra : 0;
@@ -718,7 +731,8 @@ bool same_config(const iso_workspace* ws, const iso_query_opts& o) {
     return ws->kernel == kernel && ws->tpv == tpv && ws->grid == ws->g->num_sms * per_sm &&
            ws->fuse_width == fuse && ws->use_graph == (o.use_cuda_graph != 0) && ws->timeout_ns == timeout &&
            ws->bar_extra == o.debug_barrier_extra && ws->record_trace == (o.record_trace != 0 && kernel == 1) &&
-           ws->sched_delay == (o.schedule_delay > 0 ? o.schedule_delay : 2 * ws->g->num_sms * per_sm);
+           ws->sched_delay == (o.schedule_delay > 0 ? o.schedule_delay : 2 * ws->g->num_sms * per_sm) &&
+           ws->solo_width == (o.solo_width < 0 ? 0 : (o.solo_width > 0 ? o.solo_width : kSoloWidth));
 }
 }  // namespace
 

@@ -72,9 +72,9 @@ struct SweepParams {
     int bar_extra;             // testing: extra arrivals a barrier waits for
     long long* trace;          // nullable: global ns; layout depends on the kernel (see iso_api.cu)
     // TMA kernel: chunk schedule (see schedule.cpp) and its progress
-    const int4* sched_info;    // [Q] {v0, v1, level block, mode} per schedule position
-    const int32_t* pred_off;   // [Q+1] positions each position depends on ...
-    const int32_t* pred;       // ... pred[pred_off[q] .. pred_off[q+1])
+    const int4* sched_info;    // [2Q] per schedule position {v0, v1, level block, mode},
+                               //      {first staged arc, arcs, dependency list start, its length}
+    const int32_t* pred;       // dependency lists (positions), each 16-byte aligned
     int32_t* done;             // [Q] 1 once a position is complete; zeroed per batch
     int Q;
     unsigned long long* upmask;// [n] lanes with an upward label (TMA kernel)

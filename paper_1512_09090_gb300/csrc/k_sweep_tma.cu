@@ -14,18 +14,22 @@
 // the order of a host-built schedule (schedule.cpp) that interleaves levels
 // region by region for L2 reuse; schedule position q belongs to CTA q mod G.
 // Each CTA (1024 threads, one per SM) has 31 consumer warps and one producer
-// warp.
-// The producer walks the CTA's chunks and copies each chunk's CSR offsets and
-// its contiguous block of incoming downward arcs into one of kStages shared-
-// memory buffers with cp.async.bulk, completing on the buffer's "full"
-// mbarrier; consumers release a buffer on its "empty" mbarrier, and the last
-// consumer warp to finish a chunk marks its position complete.  There are no
-// grid barriers: after starting the copy of chunk q (read-only graph data) the
-// producer warp waits until every position q depends on is complete and posts
-// that in shared memory; only then do the consumers gather the label rows d[u]
-// of q, with ld.global.cg.  Narrow levels use a warp per vertex: its groups of TPV
-// threads take every (32/TPV)-th arc, so a vertex with many arcs needs one
-// round of gathers, and chunks are 31 vertices so more CTAs share the level.
+// warp, and holds up to kStages chunks at once.
+// The producer copies each chunk's CSR offsets and its contiguous block of
+// incoming downward arcs into a free stage buffer with cp.async.bulk
+// (completing on the stage's "full" mbarrier) and caches the chunk's list of
+// dependencies (the schedule positions holding sources of its arcs) in shared
+// memory.  It never blocks: each pass it fills every free buffer, then reads
+// the completion flags of all staged chunks in one batch of relaxed loads and
+// posts every chunk whose dependencies are all complete as ready.  Each
+// consumer warp works on any ready chunk among the oldest kStages it has not
+// done (oldest first), gathering rows d[u] with ld.global.cg, so one chunk
+// waiting for another CTA does not hold up the chunks behind it.  A warp
+// releases the buffer on the "empty" mbarrier; the last of the 31 to finish a
+// chunk marks its position complete.  There are no grid barriers.
+// Narrow levels use a warp per vertex: its groups of TPV threads take every
+// (32/TPV)-th arc, so a vertex with many arcs needs one round of gathers, and
+// chunks are 31 vertices so more CTAs share the level.
 //
 // Every wait (mbarrier, dependency flags) is bounded: past the limit
 // the kernel records kStTimeout, stops issuing copies, waits (bounded) for the
@@ -38,9 +42,10 @@ using namespace isod;
 
 constexpr int kThreads = 1024;
 constexpr int kConsumers = 992;          // warps 0..30; warp 31 produces
-constexpr int kStages = 3;
-constexpr int kArcCap = 4096;            // arcs per stage buffer
+constexpr int kStages = 6;               // chunks a CTA holds at once; warps take any ready one
+constexpr int kArcCap = 1536;            // arcs per stage buffer (larger chunks read arcs from HBM)
 constexpr int kOffCap = 1024;            // offsets per stage buffer (>= VPB + 5)
+constexpr int kPredCap = 128;            // dependency list held per stage (longer lists stay in HBM)
 
 template <int K> struct MaskOf { using T = uint8_t; };
 template <> struct MaskOf<16> { using T = uint16_t; };
@@ -50,7 +55,8 @@ template <> struct MaskOf<64> { using T = unsigned long long; };
 struct Meta {
     int v0, v1;   // vertices [v0, v1)
     int abase;    // first arc index held in the stage buffer
-    int flags;    // bit 0: arcs did not fit (read them from global memory); bit 1: warp per vertex
+    int flags;    // bit 0: arcs did not fit (read them from global memory); bits 1-2: mode
+                  // (0 a thread group per vertex, 1 a warp per vertex, 2 the top block)
     int q, level; // schedule position and level block
     int pad[2];
 };
@@ -62,9 +68,9 @@ struct Smem {
     Meta meta[kStages];
     unsigned long long full[kStages];
     unsigned long long empty[kStages];
+    int32_t preds[kStages][kPredCap];  // positions the staged chunk depends on
     int finished[kStages];  // consumer warps done with the chunk in each stage
     int ready_it[kStages];  // chunk (CTA-local index + 1) whose dependencies were seen complete
-    int ok;
 };
 
 __device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -83,6 +89,19 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* b, uint32_t pa
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(sa(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Non-blocking probe of phase `parity` (try_wait may suspend the thread for a
+// while; a polling loop that also watches other things must not).
+__device__ __forceinline__ bool mbar_test_wait(unsigned long long* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
         : "r"(sa(b)), "r"(parity)
@@ -134,6 +153,29 @@ __device__ __forceinline__ Row<LPT> load_row(const uint32_t* row, int sub) {
     return r;
 }
 
+// The same through L1 (for rows nobody else writes meanwhile).
+template <int LPT, int TPV>
+__device__ __forceinline__ Row<LPT> load_row_l1(const uint32_t* row, int sub) {
+    Row<LPT> r;
+    if constexpr (LPT >= 4) {
+#pragma unroll
+        for (int q = 0; q < LPT / 4; ++q) {
+            const uint4 v = __ldca(reinterpret_cast<const uint4*>(row) + sub + TPV * q);
+            r.x[4 * q] = v.x; r.x[4 * q + 1] = v.y; r.x[4 * q + 2] = v.z; r.x[4 * q + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < LPT; ++q) r.x[q] = __ldca(row + sub * LPT + q);
+    }
+    return r;
+}
+
+// Starts pulling `bytes` (a multiple of 4) from p into L1.
+__device__ __forceinline__ void prefetch_l1(const uint32_t* p, int bytes) {
+    for (int o = 0; o < bytes; o += 128)
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(p + o / 4));
+}
+
 template <int LPT, int TPV>
 __device__ __forceinline__ void store_row(uint32_t* row, int sub, const Row<LPT>& r) {
     if constexpr (LPT >= 4) {
@@ -154,65 +196,13 @@ __device__ __forceinline__ int lane_of(int sub, int i) {
     else return sub * LPT + i;
 }
 
-// The CTA's chunks: schedule position q belongs to CTA q mod G, and every CTA
-// takes its positions in increasing order.  Both warp roles walk this order.
-struct ChunkWalk {
-    const SweepParams& p;
-    int q;
-    __device__ explicit ChunkWalk(const SweepParams& pp) : p(pp), q(blockIdx.x) {}
-    // Next chunk: vertices [v0, v1) of level block blk at position pos, with a
-    // thread group (mode 0) or a warp (mode 1) per vertex.  false at the end.
-    __device__ bool next(int& v0, int& v1, int& blk, int& mode, int& pos) {
-        if (q >= p.Q) return false;
-        const int4 c = p.sched_info[q];
-        v0 = c.x; v1 = c.y; blk = c.z; mode = c.w; pos = q;
-        q += gridDim.x;
-        return true;
-    }
-};
-
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* a) {
+// Polling load of a completion flag.  Flags are read relaxed, so that all of a
+// pass's loads are in flight at once; the reader fences (acquire) once after
+// seeing every flag it needs set.
+__device__ __forceinline__ uint32_t ld_relaxed(const int32_t* a) {
     uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a));
     return v;
-}
-
-// Bounded wait, by a whole warp, until every position schedule position q
-// depends on is complete (plus bar_extra flags that never come when a test asks
-// for a timeout).  Returns false, the same on every lane, if it gave up.
-__device__ bool wait_deps(const SweepParams& p, int q, int lane) {
-    const int a = p.pred_off[q], b_real = p.pred_off[q + 1], b = b_real + p.bar_extra;
-    const unsigned long long t0 = global_ns();
-    for (int base = a; base < b; base += 128) {
-        // up to four flags per lane, all loads in flight at once
-        bool mine[4];
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int i = base + lane + 32 * t;
-            mine[t] = i >= b || (i < b_real && ld_acquire(reinterpret_cast<const uint32_t*>(p.done + p.pred[i])) != 0u);
-        }
-        uint32_t nap = 32;
-        for (uint32_t it = 0; !__all_sync(0xffffffffu, mine[0] && mine[1] && mine[2] && mine[3]); ++it) {
-            __nanosleep(nap);
-            if (nap < 256) nap <<= 1;
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const int i = base + lane + 32 * t;
-                if (!mine[t] && i < b_real)
-                    mine[t] = ld_acquire(reinterpret_cast<const uint32_t*>(p.done + p.pred[i])) != 0u;
-            }
-            int give_up = 0;
-            if (lane == 0 && (it & 15) == 15) {
-                if (*(volatile int32_t*)p.status != kStOk) give_up = 1;
-                else if (global_ns() - t0 > (unsigned long long)p.timeout_ns || it > (1u << 26)) {
-                    atomicCAS(p.status, kStOk, kStTimeout);
-                    give_up = 1;
-                }
-            }
-            if (__shfl_sync(0xffffffffu, give_up, 0)) return false;
-        }
-    }
-    return true;
 }
 
 // Gathers rows d[u] + len(u,v) for arcs a, a+STEP, a+2*STEP, ... < e into acc.
@@ -240,31 +230,149 @@ __device__ __forceinline__ void gather(Row<LPT>& acc, const uint32_t* d, const i
     }
 }
 
-// Starts pulling the rows of arcs a, a+step, ... < e into L2 (no registers, no
-// shared memory: cp.async.bulk.prefetch).  Stale or not-yet-final rows are
-// harmless there: every later store lands in L2 as well.
-__device__ __forceinline__ void prefetch_rows(const uint32_t* d, int K, const int2* arcs, uint32_t a, uint32_t e,
-                                              uint32_t step) {
-    const uint32_t bytes = (uint32_t)K * 4u;
-    for (; a < e; a += step) {
-        const uint32_t* row = d + (size_t)arcs[a].x * K;
-        if (bytes >= 16)
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(row), "r"(bytes) : "memory");
-        else
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(row) : "memory");
+// True (on every lane) if every position in pred[pa .. pa+np) is complete right
+// now (plus bar_extra flags that never come when a test asks for a timeout).
+// Relaxed reads: the caller fences before relying on the result.
+__device__ bool deps_done_now(const SweepParams& p, int pa, int np, int lane) {
+    const int b_real = pa + np, b = b_real + p.bar_extra;
+    for (int i = pa + lane;; i += 32) {
+        const bool mine = i >= b || (i < b_real && ld_relaxed(p.done + p.pred[i]) != 0u);
+        if (!__all_sync(0xffffffffu, mine)) return false;
+        if (__all_sync(0xffffffffu, i + 32 >= b)) return true;
+    }
+}
+
+// New label row of vertex v: min(upward labels, min over its downward arcs
+// [a, e) of d[u] + len), pruned at tau; stored as a row (if `store`) and as an
+// in-range mask.  WPV: the whole warp works on v, its 32/TPV groups of TPV
+// threads taking every (32/TPV)-th arc; otherwise v belongs to one group.  With
+// a warp per vertex (narrow levels, where the sweep waits on latency) the
+// vertex's own state is read before the gathers instead of after them.
+template <int K, int TPV, bool WPV>
+__device__ __forceinline__ void vertex_update(const SweepParams& p, const Smem& sm, int v, bool valid, uint32_t a,
+                                              uint32_t e, const int2* arcs, bool store, int tid) {
+    constexpr int LPT = K / TPV;
+    constexpr int GPV = 32 / TPV;
+    using MaskT = typename MaskOf<K>::T;
+    const int lane = tid & 31;
+    const int sub = tid % TPV;
+    const int g = WPV ? lane / TPV : 0;
+    Row<LPT> acc;
+#pragma unroll
+    for (int i = 0; i < LPT; ++i) acc.x[i] = kInf;
+    unsigned long long um = 0;
+    bool hit = false;
+    if (WPV) {
+        // the row of v is written by nobody but this update during the sweep,
+        // so an L1 copy of it cannot be stale
+        if (valid && g == 0) {
+            um = __ldcg(p.upmask + v);
+            prefetch_l1(p.d + (size_t)v * K, K * 4);
+        }
+        if (valid) gather<K, LPT, TPV, GPV>(acc, p.d, arcs, a + g, e, sub);
+#pragma unroll
+        for (int o = TPV; o < 32; o <<= 1) {
+#pragma unroll
+            for (int i = 0; i < LPT; ++i) acc.x[i] = min(acc.x[i], __shfl_xor_sync(0xffffffffu, acc.x[i], o));
+        }
+        hit = um != 0ull;
+    } else if (valid) {
+        hit = __ldcg(p.upflag + v) != 0;
+        gather<K, LPT, TPV, 1>(acc, p.d, arcs, a, e, sub);
+        if (hit) um = __ldcg(p.upmask + v);
+    }
+    if (hit) {
+        // upward labels: only the lanes marked in upmask hold this batch's values
+        const Row<LPT> own = WPV ? load_row_l1<LPT, TPV>(p.d + (size_t)v * K, sub)
+                                 : load_row<LPT, TPV>(p.d + (size_t)v * K, sub);
+#pragma unroll
+        for (int i = 0; i < LPT; ++i)
+            if ((um >> lane_of<LPT, TPV>(sub, i)) & 1ull) acc.x[i] = min(acc.x[i], own.x[i]);
+    }
+    __syncwarp();  // every thread of the vertex has read flag and mask before they are cleared
+    if (hit && g == 0 && sub == 0) { p.upflag[v] = 0; p.upmask[v] = 0ull; }
+    unsigned long long bits = 0;
+#pragma unroll
+    for (int i = 0; i < LPT; ++i) {
+        const int ln = lane_of<LPT, TPV>(sub, i);
+        if (acc.x[i] > sm.tau[ln]) acc.x[i] = kInf;
+        else bits |= 1ull << ln;
+    }
+    if (valid && store && g == 0) store_row<LPT, TPV>(p.d + (size_t)v * K, sub, acc);
+#pragma unroll
+    for (int o = 1; o < TPV; o <<= 1) bits |= __shfl_xor_sync(0xffffffffu, bits, o);
+    if (valid && sub == 0 && g == 0) static_cast<MaskT*>(p.mask)[v] = (MaskT)bits;
+}
+
+// The top block (levels 0..last), swept level by level by all consumer warps
+// of CTA 0 together, with a named barrier after each level.  They run it first
+// thing, unconditionally: it needs no staged data and depends on nothing, so
+// every consumer warp reaches every barrier.
+template <int K, int TPV>
+__device__ void process_top_block(const SweepParams& p, const Smem& sm, int last, int warp, int tid) {
+    for (int j = 0; j <= last; ++j) {
+        const int lo = __ldg(p.level_off + j), hi = __ldg(p.level_off + j + 1);
+        const bool store = p.write_all || j != p.last_level_block;
+        for (int v = lo + warp; v < hi; v += kConsumers / 32)
+            vertex_update<K, TPV, true>(p, sm, v, true, __ldg(p.down_off + v), __ldg(p.down_off + v + 1), p.down_arc,
+                                        store, tid);
+        asm volatile("bar.sync 1, 992;" ::: "memory");
+        if (p.trace && tid == 0) atomicMax((unsigned long long*)p.trace + 1 + j, global_ns());
+    }
+}
+
+// The chunk held in `stage`, by one consumer warp (its share of the vertices).
+template <int K, int TPV>
+__device__ __forceinline__ void process_chunk(const SweepParams& p, const Smem& sm, int stage, int warp, int tid) {
+    const Meta mt = sm.meta[stage];
+    const int mode = (mt.flags >> 1) & 1;
+    const int ob = mt.v0 & ~3;
+    const int v = mode ? mt.v0 + warp : mt.v0 + tid / TPV;
+    const bool valid = v < mt.v1;
+    const bool store = p.write_all || mt.level != p.last_level_block;
+    uint32_t a = 0, e = 0;
+    if (valid) {
+        a = sm.offs[stage][v - ob];
+        e = sm.offs[stage][v + 1 - ob];
+    }
+    const int2* arcs = (mt.flags & 1) ? p.down_arc : sm.arcs[stage] - mt.abase;
+    if (mode) vertex_update<K, TPV, true>(p, sm, v, valid, a, e, arcs, store, tid);
+    else vertex_update<K, TPV, false>(p, sm, v, valid, a, e, arcs, store, tid);
+}
+
+// A consumer warp is done with the chunk in `stage` (schedule position q, level
+// block `level`): the last of the consumer warps to get here publishes the
+// position as complete to every CTA; each warp releases the buffer.
+__device__ __forceinline__ void release_chunk(const SweepParams& p, Smem& sm, int stage, int q, int level, int lane) {
+    __syncwarp();
+    if (lane == 0) {
+        __threadfence_block();
+        if (atomicAdd(&sm.finished[stage], 1) == kConsumers / 32 - 1) {
+            __threadfence_block();
+            sm.finished[stage] = 0;
+            __threadfence();
+            *(volatile int32_t*)(p.done + q) = 1;
+            if (p.trace) atomicMax((unsigned long long*)p.trace + 1 + level, global_ns());
+        }
+        mbar_arrive(&sm.empty[stage]);
     }
 }
 
 template <int K, int TPV>
 __global__ void __launch_bounds__(kThreads, 1) k_sweep_tma(SweepParams p) {
-    constexpr int LPT = K / TPV;
     constexpr int VPB = kConsumers / TPV;
     static_assert(VPB + 5 <= kOffCap, "offset buffer");
-    using MaskT = typename MaskOf<K>::T;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
+    // chunks of this CTA: positions blockIdx.x, blockIdx.x + G, ...
+    const int G = (int)gridDim.x;
+    const int n_mine = (int)blockIdx.x < p.Q ? (p.Q - (int)blockIdx.x + G - 1) / G : 0;
+    // position 0 may be the top block (mode 2); it is CTA 0's chunk 0 and is
+    // never staged: stage 0 starts with chunk kStages, one phase later
+    const int4 head = p.Q > 0 ? __ldg(p.sched_info) : make_int4(0, 0, 0, 0);
+    const bool top = blockIdx.x == 0 && p.Q > 0 && head.w == 2;
 
     if (tid == 0) {
         for (int i = 0; i < kStages; ++i) {
@@ -275,160 +383,177 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tma(SweepParams p) {
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    if (tid < K) {
+        const int32_t t = p.tau[tid];
+        sm.tau[tid] = t < 0 ? 0u : (uint32_t)t;
+    }
+    if (p.trace && tid == 0 && blockIdx.x == 0) p.trace[0] = p.trace[p.L + 1] = (long long)global_ns();
     __syncthreads();
 
     if (warp == kConsumers / 32) {
-        // ---------------- producer warp: checks dependencies, copies chunks ----------------
-        ChunkWalk walk(p);
-        int it = 0;
-        int v0, v1, blk, mode, pos;
-        while (walk.next(v0, v1, blk, mode, pos)) {
-            const int stage = it % kStages;
-            const uint32_t round = (uint32_t)(it / kStages);
-            int fine = 1;
-            if (lane == 0) fine = mbar_wait(&sm.empty[stage], (round & 1u) ^ 1u, p);
-            fine = __shfl_sync(0xffffffffu, fine, 0);
-            if (!fine) break;
+        // ---------------- producer warp ----------------
+        // Lane s < kStages runs stage s, whose chunks are s, s + kStages, ...:
+        // once the stage is free it copies the next one's offsets, arcs and
+        // dependency list in, and once those have landed and every position
+        // the chunk depends on is complete it posts the chunk as ready.  No
+        // lane ever blocks, so the stages' latencies overlap.
+        int t = lane;             // next chunk of my stage
+        int cur = -1;             // chunk in my stage not posted yet, or -1
+        int cur_pa = 0, cur_np = 0;
+        bool cur_held = false;    // its dependency list was copied to shared memory
+        int posted = 0;
+        if (top) {
             if (lane == 0) {
-                const uint32_t off0 = __ldg(p.down_off + v0), off1 = __ldg(p.down_off + v1);
-                const int ob = v0 & ~3;
-                const uint32_t obytes = (uint32_t)(((v1 + 1 - ob) * 4 + 15) & ~15);
-                const uint32_t ab = off0 & ~1u;
-                const uint32_t na = off1 - ab;
-                const bool big = na > (uint32_t)kArcCap;
-                const uint32_t abytes = big ? 0u : ((na * 8u + 15u) & ~15u);
-                sm.meta[stage] = Meta{v0, v1, (int)ab, (big ? 1 : 0) | (mode ? 2 : 0), pos, blk, {0, 0}};
-                mbar_expect_tx(&sm.full[stage], obytes + abytes);
-                bulk_load(sm.offs[stage], p.down_off + ob, obytes, &sm.full[stage]);
-                if (abytes) bulk_load(sm.arcs[stage], p.down_arc + ab, abytes, &sm.full[stage]);
+                mbar_arrive(&sm.full[0]);  // phase 0 of stage 0 stands for the top block
+                t = kStages;
             }
-            __syncwarp();
-            ++it;
-            // the copy is in flight; meanwhile wait for the chunk's dependencies
-            // and tell the consumers when its rows may be gathered
-            if (!wait_deps(p, pos, lane)) break;
-            __threadfence_block();
-            if (lane == 0) *(volatile int*)&sm.ready_it[stage] = it;
+            posted = 1;
+        }
+        unsigned long long last_progress = global_ns();
+        uint32_t nap = 32;
+        while (posted < n_mine) {
+            // (1) copy the next chunk into every free stage
+            const bool issue = lane < kStages && cur < 0 && t < n_mine &&
+                               (t < kStages || mbar_test_wait(&sm.empty[lane], ((uint32_t)(t / kStages) & 1u) ^ 1u));
+            if (issue) {
+                const int pos = (int)blockIdx.x + t * G;
+                const int4 c0 = __ldg(p.sched_info + 2 * (size_t)pos);      // v0, v1, level, mode
+                const int4 c1 = __ldg(p.sched_info + 2 * (size_t)pos + 1);  // arc base, arcs, deps start, deps
+                const int ob = c0.x & ~3;
+                uint32_t obytes = 0, abytes = 0;
+                int big = 0;
+                if (c0.w != 2) {
+                    obytes = (uint32_t)(((c0.y + 1 - ob) * 4 + 15) & ~15);
+                    big = c1.y > kArcCap;
+                    abytes = big ? 0u : (uint32_t)((c1.y * 8 + 15) & ~15);
+                }
+                cur_held = c1.w <= kPredCap && p.bar_extra == 0;
+                const uint32_t pbytes = cur_held ? (uint32_t)(((c1.w + 3) & ~3) * 4) : 0u;
+                sm.meta[lane] = Meta{c0.x, c0.y, c1.x, big | (c0.w << 1), pos, c0.z, {0, 0}};
+                mbar_expect_tx(&sm.full[lane], obytes + abytes + pbytes);
+                if (obytes) bulk_load(sm.offs[lane], p.down_off + ob, obytes, &sm.full[lane]);
+                if (abytes) bulk_load(sm.arcs[lane], p.down_arc + c1.x, abytes, &sm.full[lane]);
+                if (pbytes) bulk_load(sm.preds[lane], p.pred + c1.z, pbytes, &sm.full[lane]);
+                cur = t;
+                cur_pa = c1.z;
+                cur_np = c1.w;
+                t += kStages;
+            }
+            bool progress = __any_sync(0xffffffffu, issue);
+            // (2) post the staged chunks whose copies have landed and whose
+            // dependencies are complete: one pass reads the flags of all of
+            // them, every load in flight at once
+            const bool landed =
+                lane < kStages && cur >= 0 && mbar_test_wait(&sm.full[lane], (uint32_t)(cur / kStages) & 1u);
+            const uint32_t cand = __ballot_sync(0xffffffffu, landed);
+            if (cand) {
+                uint32_t notdone = 0;
+#pragma unroll
+                for (int st = 0; st < kStages; ++st) {
+                    if (!((cand >> st) & 1u)) continue;
+                    const int cst = __shfl_sync(0xffffffffu, cur, st);
+                    const int np = __shfl_sync(0xffffffffu, cur_np, st);
+                    const int pa = __shfl_sync(0xffffffffu, cur_pa, st);
+                    if (!__shfl_sync(0xffffffffu, (int)cur_held, st)) {
+                        if (!deps_done_now(p, pa, np, lane)) notdone |= 1u << st;
+                        continue;
+                    }
+                    // this lane's view of the landed copy (the phase cannot move on yet)
+                    (void)mbar_test_wait(&sm.full[st], (uint32_t)(cst / kStages) & 1u);
+#pragma unroll
+                    for (int r = 0; r < kPredCap / 32; ++r) {
+                        const int i = lane + 32 * r;
+                        if (i < np && ld_relaxed(p.done + sm.preds[st][i]) == 0u) notdone |= 1u << st;
+                    }
+                }
+                notdone = __reduce_or_sync(0xffffffffu, notdone);
+                const uint32_t now_ready = cand & ~notdone;
+                if (now_ready) {
+                    __threadfence();  // acquire: the flags seen set order the label rows behind them
+                    if ((now_ready >> lane) & 1u) {
+                        *(volatile int*)&sm.ready_it[lane] = cur + 1;
+                        cur = -1;
+                    }
+                    posted += __popc(now_ready);
+                    progress = true;
+                }
+            }
+            if (progress) {
+                nap = 32;
+                last_progress = global_ns();
+                continue;
+            }
+            __nanosleep(nap);
+            if (nap < 256) nap <<= 1;
+            int give_up = 0;
+            if (lane == 0) {
+                if (*(volatile int32_t*)p.status != kStOk) give_up = 1;
+                else if (global_ns() - last_progress > (unsigned long long)p.timeout_ns) {
+                    atomicCAS(p.status, kStOk, kStTimeout);
+                    give_up = 1;
+                }
+            }
+            if (__shfl_sync(0xffffffffu, give_up, 0)) break;
         }
         // every issued copy must land before the CTA exits
-        if (lane == 0)
-            for (int i = it > kStages ? it - kStages : 0; i < it; ++i)
-                mbar_wait(&sm.full[i % kStages], (uint32_t)(i / kStages) & 1u, p);
+        if (lane < kStages && t >= kStages) {
+            const int last = t - kStages;
+            mbar_wait(&sm.full[lane], (uint32_t)(last / kStages) & 1u, p);
+        }
         __syncthreads();
         return;
     }
 
     // ---------------- consumer warps ----------------
-    // mode 0: a group of TPV threads per vertex; mode 1: a warp per vertex whose
-    // GPV groups take every GPV-th arc and then combine with shuffles
-    constexpr int GPV = 32 / TPV;
-    const int sub = tid % TPV;
-    if (tid < K) {
-        const int32_t t = p.tau[tid];
-        sm.tau[tid] = t < 0 ? 0u : (uint32_t)t;
+    // Each warp takes, among the oldest kStages chunks it has not done yet, any
+    // one that is copied and ready (oldest first), does its part of it, and
+    // releases the buffer; the last warp to finish a chunk publishes it.
+    int base = 0;            // oldest chunk this warp has not done
+    uint32_t done_bits = 0;  // bit d: chunk base + d done by this warp
+    if (top) {
+        process_top_block<K, TPV>(p, sm, head.z, warp, tid);
+        release_chunk(p, sm, 0, 0, head.z, lane);
+        base = 1;
     }
-    if (tid == 0) sm.ok = 0;  // positions below sm.ok are known complete
-    asm volatile("bar.sync 1, 992;" ::: "memory");
-    if (p.trace && tid == 0 && blockIdx.x == 0) p.trace[0] = p.trace[p.L + 1] = (long long)global_ns();
-
-    ChunkWalk walk(p);
-    bool alive = true;
-    int it = 0;
-    int v0, v1, j, mode, pos;
-    while (walk.next(v0, v1, j, mode, pos)) {
-        const int stage = it % kStages;
-        const uint32_t round = (uint32_t)(it / kStages);
-        ++it;
-        // the producer posts ready_it once every position the chunk depends on is
-        // complete; only then may its rows be gathered
-        if (alive && lane == 0) {
-            const unsigned long long t0 = global_ns();
-            for (uint32_t n = 0; *(volatile int*)&sm.ready_it[stage] != it; ++n) {
-                __nanosleep(32);
-                if ((n & 255) == 255 && (*(volatile int32_t*)p.status != kStOk ||
-                                         global_ns() - t0 > (unsigned long long)p.timeout_ns)) {
+    unsigned long long last_progress = global_ns();
+    uint32_t nap = 32;
+    while (base < n_mine) {
+        // lane d looks at chunk base + d of the window
+        bool cand = false;
+        if (lane < kStages && base + lane < n_mine && !((done_bits >> lane) & 1u)) {
+            const int t = base + lane;
+            const int stage = t % kStages;
+            cand = *(volatile int*)&sm.ready_it[stage] == t + 1 &&
+                   mbar_test_wait(&sm.full[stage], (uint32_t)(t / kStages) & 1u);
+        }
+        const uint32_t ready = __ballot_sync(0xffffffffu, cand);
+        if (!ready) {
+            __nanosleep(nap);
+            if (nap < 256) nap <<= 1;
+            int give_up = 0;
+            if (lane == 0) {
+                if (*(volatile int32_t*)p.status != kStOk) give_up = 1;
+                else if (global_ns() - last_progress > (unsigned long long)p.timeout_ns) {
                     atomicCAS(p.status, kStOk, kStTimeout);
-                    alive = false;
-                    break;
+                    give_up = 1;
                 }
             }
+            if (__shfl_sync(0xffffffffu, give_up, 0)) break;
+            continue;
         }
-        alive = __shfl_sync(0xffffffffu, alive, 0);
+        nap = 32;
+        last_progress = global_ns();
+        const int pick = __ffs(ready) - 1;
+        const int t = base + pick;
+        const int stage = t % kStages;
+        // every lane acquires the copied data (the phase is complete and cannot
+        // move on before this warp releases the buffer) and the ready flag
+        mbar_wait(&sm.full[stage], (uint32_t)(t / kStages) & 1u, p);
         __threadfence_block();
-        const bool ready = __all_sync(0xffffffffu, alive && mbar_wait(&sm.full[stage], round & 1u, p));
-        if (ready) {
-            const Meta mt = sm.meta[stage];
-            const int ob = mt.v0 & ~3;
-            const int g = mode ? lane / TPV : 0;         // arc group within the vertex
-            const int v = mode ? v0 + warp : v0 + tid / TPV;
-            const bool valid = v < v1;
-            const bool store = p.write_all || j != p.last_level_block;
-            Row<LPT> acc;
-#pragma unroll
-            for (int i = 0; i < LPT; ++i) acc.x[i] = kInf;
-            uint32_t a = 0, e = 0, flagged = 0;
-            if (valid) {
-                flagged = __ldcg(p.upflag + v);
-                a = sm.offs[stage][v - ob] + g;
-                e = sm.offs[stage][v + 1 - ob];
-            }
-            const int2* arcs = (mt.flags & 1) ? p.down_arc : sm.arcs[stage] - mt.abase;
-            // the CTA's next chunk is usually staged already: warm L2 with its rows
-            if (sub == 0 && mbar_try_wait(&sm.full[it % kStages], (uint32_t)(it / kStages) & 1u)) {
-                const Meta nx = sm.meta[it % kStages];
-                const int nm = (nx.flags >> 1) & 1;
-                const int nv = nm ? nx.v0 + warp : nx.v0 + tid / TPV;
-                if (nv < nx.v1 && !(nx.flags & 1)) {
-                    const int nob = nx.v0 & ~3;
-                    const uint32_t* noffs = sm.offs[it % kStages];
-                    prefetch_rows(p.d, K, sm.arcs[it % kStages] - nx.abase, noffs[nv - nob] + (nm ? lane / TPV : 0),
-                                  noffs[nv + 1 - nob], nm ? GPV : 1);
-                }
-            }
-            if (mode) gather<K, LPT, TPV, GPV>(acc, p.d, arcs, a, e, sub);
-            else gather<K, LPT, TPV, 1>(acc, p.d, arcs, a, e, sub);
-            if (mode) {
-#pragma unroll
-                for (int o = TPV; o < 32; o <<= 1) {
-#pragma unroll
-                    for (int i = 0; i < LPT; ++i) acc.x[i] = min(acc.x[i], __shfl_xor_sync(0xffffffffu, acc.x[i], o));
-                }
-            }
-            if (flagged) {
-                // upward labels: only the lanes marked in upmask hold this batch's values
-                const unsigned long long um = __ldcg(p.upmask + v);
-                const Row<LPT> own = load_row<LPT, TPV>(p.d + (size_t)v * K, sub);
-#pragma unroll
-                for (int i = 0; i < LPT; ++i)
-                    if ((um >> lane_of<LPT, TPV>(sub, i)) & 1ull) acc.x[i] = min(acc.x[i], own.x[i]);
-            }
-            __syncwarp();  // every thread of the vertex has read flag and mask before they are cleared
-            if (flagged && g == 0 && sub == 0) { p.upflag[v] = 0; p.upmask[v] = 0ull; }
-            unsigned long long bits = 0;
-#pragma unroll
-            for (int i = 0; i < LPT; ++i) {
-                const int ln = lane_of<LPT, TPV>(sub, i);
-                if (acc.x[i] > sm.tau[ln]) acc.x[i] = kInf;
-                else bits |= 1ull << ln;
-            }
-            if (valid && store && g == 0) store_row<LPT, TPV>(p.d + (size_t)v * K, sub, acc);
-#pragma unroll
-            for (int o = 1; o < TPV; o <<= 1) bits |= __shfl_xor_sync(0xffffffffu, bits, o);
-            if (valid && sub == 0 && g == 0) static_cast<MaskT*>(p.mask)[v] = (MaskT)bits;
-        }
-        __syncwarp();
-        if (lane == 0) {
-            // the last warp to finish the chunk publishes it to the other CTAs
-            __threadfence_block();
-            if (atomicAdd(&sm.finished[stage], 1) == kConsumers / 32 - 1) {
-                __threadfence_block();
-                sm.finished[stage] = 0;
-                __threadfence();
-                *(volatile int32_t*)(p.done + pos) = 1;
-                if (p.trace) atomicMax((unsigned long long*)p.trace + 1 + j, global_ns());
-            }
-            mbar_arrive(&sm.empty[stage]);
-        }
+        process_chunk<K, TPV>(p, sm, stage, warp, tid);
+        release_chunk(p, sm, stage, sm.meta[stage].q, sm.meta[stage].level, lane);
+        done_bits |= 1u << pick;
+        while (done_bits & 1u) { done_bits >>= 1; ++base; }
     }
     __syncthreads();
 }

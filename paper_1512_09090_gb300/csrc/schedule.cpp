@@ -13,8 +13,14 @@
 // becomes eligible `delay` positions after its last dependency, so that the
 // device rarely has to wait for one.
 //
-// For position q the device receives {v0, v1, level block, mode} and the list
-// of positions q depends on; it starts chunk q once all of them are complete.
+// The top levels of the hierarchy hold few vertices each but form a long chain
+// of dependencies; run as separate chunks, every level would cost a round trip
+// between CTAs.  The first `solo_levels` levels are therefore one chunk, which
+// a single CTA sweeps level by level with CTA barriers; it is scheduled first.
+//
+// For position q the device receives its chunk's vertex and arc ranges and the
+// list of positions q depends on; it starts chunk q once all of them are
+// complete.
 #include <algorithm>
 #include <cstdint>
 #include <queue>
@@ -24,13 +30,17 @@
 #include "sweep_schedule.h"
 
 int iso_make_schedule(int n, int L, const int32_t* level_off, const uint32_t* down_off, const int32_t* down_src,
-                      const int32_t* bfs, int vpb, int narrow_chunk, int narrow_width, int delay,
+                      const int32_t* bfs, int vpb, int narrow_chunk, int narrow_width, int solo_levels, int delay,
                       SweepSchedule* out) {
-    if (n <= 0 || L <= 0 || vpb <= 0 || narrow_chunk <= 0) return -1;
+    if (n <= 0 || L <= 0 || vpb <= 0 || narrow_chunk <= 0 || solo_levels < 0 || solo_levels > L) return -1;
     // chunks in level order
     std::vector<int32_t> cv0, cv1, clev, cmode;
     std::vector<int32_t> chunk_of(n);
-    for (int j = 0; j < L; ++j) {
+    if (solo_levels > 0) {
+        cv0.push_back(0); cv1.push_back(level_off[solo_levels]); clev.push_back(solo_levels - 1); cmode.push_back(2);
+        for (int v = 0; v < level_off[solo_levels]; ++v) chunk_of[v] = 0;
+    }
+    for (int j = solo_levels; j < L; ++j) {
         const int lo = level_off[j], hi = level_off[j + 1];
         const int mode = narrow_width > 0 && hi - lo < narrow_width ? 1 : 0;
         const int per = mode ? narrow_chunk : vpb;
@@ -56,7 +66,7 @@ int iso_make_schedule(int n, int L, const int32_t* level_off, const uint32_t* do
             for (int v = cv0[c]; v < cv1[c]; ++v)
                 for (uint32_t a = down_off[v]; a < down_off[v + 1]; ++a) {
                     const int pc = chunk_of[down_src[a]];
-                    if (mark[pc] == c) continue;
+                    if (pc == c || mark[pc] == c) continue;  // arcs inside the top block
                     mark[pc] = c;
                     if (pass == 0) { soff[pc + 1]++; indeg[c]++; }
                     else out->succ[fill[pc]++] = c;
@@ -72,7 +82,7 @@ int iso_make_schedule(int n, int L, const int32_t* level_off, const uint32_t* do
     std::vector<int64_t> earliest(Q, 0);
     std::vector<int32_t> pos_of(Q, -1);
     // spatial key, then higher level first
-    auto key = [&](int c) { return (int64_t)bfs[cv0[c]] * (L + 1) + clev[c]; };
+    auto key = [&](int c) { return cmode[c] == 2 ? (int64_t)-1 : (int64_t)bfs[cv0[c]] * (L + 1) + clev[c]; };
     for (int c = 0; c < Q; ++c)
         if (indeg[c] == 0) ready.push({key(c), c});
     out->info.resize(Q);
@@ -89,7 +99,12 @@ int iso_make_schedule(int n, int L, const int32_t* level_off, const uint32_t* do
         const int c = ready.top().second;
         ready.pop();
         pos_of[c] = q;
-        out->info[q] = {cv0[c], cv1[c], clev[c], cmode[c]};
+        out->info[q] = {cv0[c], cv1[c], clev[c], cmode[c], 0, 0, 0, 0};
+        if (cmode[c] != 2) {
+            const uint32_t ab = down_off[cv0[c]] & ~1u;
+            out->info[q].abase = (int32_t)ab;
+            out->info[q].na = (int32_t)(down_off[cv1[c]] - ab);
+        }
         for (int32_t i = soff[c]; i < soff[c + 1]; ++i) {
             const int s = out->succ[i];
             earliest[s] = std::max<int64_t>(earliest[s], (int64_t)q + delay);
@@ -113,16 +128,22 @@ int iso_make_schedule(int n, int L, const int32_t* level_off, const uint32_t* do
         for (int32_t p : preds[c])
             if (implied[p] != c) kept[c].push_back(p);
     }
-    out->pred_off.assign(Q + 1, 0);
-    for (int c = 0; c < Q; ++c) out->pred_off[pos_of[c] + 1] = (int32_t)kept[c].size();
-    for (int q = 0; q < Q; ++q) out->pred_off[q + 1] += out->pred_off[q];
-    out->pred.assign(out->pred_off[Q], 0);
+    std::vector<int32_t> pred_at(Q + 1, 0);  // padded list starts by position
+    for (int c = 0; c < Q; ++c) pred_at[pos_of[c] + 1] = ((int32_t)kept[c].size() + 3) & ~3;
+    for (int q = 0; q < Q; ++q) pred_at[q + 1] += pred_at[q];
+    out->pred.assign(std::max<int32_t>(pred_at[Q], 4), 0);
     for (int c = 0; c < Q; ++c) {
-        int32_t o = out->pred_off[pos_of[c]];
-        for (int32_t p : kept[c]) {
-            if (pos_of[p] >= pos_of[c]) return -1;  // not topological: refuse
-            out->pred[o++] = pos_of[p];
+        const int q = pos_of[c];
+        const int32_t o = pred_at[q];
+        const int32_t np = (int32_t)kept[c].size();
+        for (int32_t i = 0; i < np; ++i) {
+            const int32_t pq = pos_of[kept[c][i]];
+            if (pq >= q) return -1;  // not topological: refuse
+            out->pred[o + i] = pq;
         }
+        for (int32_t i = np; i < pred_at[q + 1] - o; ++i) out->pred[o + i] = out->pred[o];
+        out->info[q].pa = o;
+        out->info[q].np = np;
     }
     out->succ.clear();
     out->succ.shrink_to_fit();

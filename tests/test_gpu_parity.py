@@ -125,6 +125,24 @@ def test_fusion_and_cuda_graph(fuse, graph, kernel):
     check_batch(g, dg, srcs, taus, fuse_width=fuse, use_cuda_graph=graph, sweep_kernel=kernel)
 
 
+@pytest.mark.parametrize("solo", [-1, 1, 124, 1 << 30])
+@pytest.mark.parametrize("graph", [0, 1])
+def test_top_block_sizes(solo, graph):
+    # -1: no top block; 1 << 30: the whole hierarchy is one block run by CTA 0
+    g, dg = dev_graph("grid64")
+    srcs = synth.draw_sources(g, 16, 15)
+    taus = synth.draw_taus_uniform(16, 0, 3000, 16)
+    check_batch(g, dg, srcs, taus, solo_width=solo, use_cuda_graph=graph, sweep_kernel=1)
+
+
+@pytest.mark.parametrize("solo", [-1, 124, 4000])
+def test_top_block_grid1k(solo):
+    g, dg = dev_graph("grid1k")
+    srcs = synth.draw_sources(g, 64, 51)
+    taus = synth.draw_taus_uniform(64, 0, 60000, 52)
+    check_batch(g, dg, srcs, taus, want_dist=True, solo_width=solo, sweep_kernel=1)
+
+
 def test_duplicate_sources_and_extreme_limits():
     g, dg = dev_graph("grid64")
     s = synth.draw_sources(g, 1, 3)[0]
