@@ -149,7 +149,7 @@ typedef struct {
     int32_t sweep_kernel;       /* 0 = auto (TMA-staged arc blocks), 1 = TMA-staged, 2 = plain loads */
     int32_t record_trace;       /* 1 = record the device time of every sweep step (iso_workspace_trace) */
     int32_t schedule_delay;     /* TMA-staged sweep: a chunk is scheduled at least this many positions
-                                   after the chunks it depends on; 0 = auto (twice the CTA count) */
+                                   after the chunks it depends on; 0 = auto (four times the CTA count) */
     int32_t solo_width;         /* TMA-staged sweep: the top levels of the hierarchy, as long as each
                                    has at most this many vertices, run in one CTA level by level
                                    (CTA barriers instead of flags between CTAs); 0 = auto (124),

@@ -512,7 +512,7 @@ extern "C" int iso_workspace_create(iso_graph* g, int32_t lanes, const iso_query
     // a level narrower than one chunk of ws->vpb vertices per CTA runs with a warp per vertex
     ws->narrow_width = o.fuse_width < 0 ? 0 : (o.fuse_width > 0 ? o.fuse_width : ws->grid * vpb);
     ws->record_trace = o.record_trace != 0 && ws->kernel == 1;
-    ws->sched_delay = o.schedule_delay > 0 ? o.schedule_delay : 2 * ws->grid;
+    ws->sched_delay = o.schedule_delay > 0 ? o.schedule_delay : 4 * ws->grid;
     ws->solo_width = o.solo_width < 0 ? 0 : (o.solo_width > 0 ? o.solo_width : kSoloWidth);
     ws->use_graph = opts ? opts->use_cuda_graph != 0 : false;
     if (opts && opts->barrier_timeout_ns) ws->timeout_ns = opts->barrier_timeout_ns;
@@ -731,7 +731,7 @@ bool same_config(const iso_workspace* ws, const iso_query_opts& o) {
     return ws->kernel == kernel && ws->tpv == tpv && ws->grid == ws->g->num_sms * per_sm &&
            ws->fuse_width == fuse && ws->use_graph == (o.use_cuda_graph != 0) && ws->timeout_ns == timeout &&
            ws->bar_extra == o.debug_barrier_extra && ws->record_trace == (o.record_trace != 0 && kernel == 1) &&
-           ws->sched_delay == (o.schedule_delay > 0 ? o.schedule_delay : 2 * ws->g->num_sms * per_sm) &&
+           ws->sched_delay == (o.schedule_delay > 0 ? o.schedule_delay : 4 * ws->g->num_sms * per_sm) &&
            ws->solo_width == (o.solo_width < 0 ? 0 : (o.solo_width > 0 ? o.solo_width : kSoloWidth));
 }
 }  // namespace

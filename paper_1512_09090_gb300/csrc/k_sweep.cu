@@ -101,10 +101,15 @@ __device__ __forceinline__ void store_row(uint32_t* ptr, const Row<LPT>& r) {
 }
 
 template <int LPT>
-__device__ __forceinline__ void relax(Row<LPT>& acc, const uint32_t* d, int K, int2 arc, int sub) {
-    const Row<LPT> r = load_row<LPT>(d + (size_t)arc.x * K + sub * LPT);
+__device__ __forceinline__ Row<LPT> load_row_if(const uint32_t* ptr, bool ok) {
+    Row<LPT> r;
+    if (ok) {
+        r = load_row<LPT>(ptr);
+    } else {
 #pragma unroll
-    for (int i = 0; i < LPT; ++i) acc.x[i] = min(acc.x[i], r.x[i] + (uint32_t)arc.y);
+        for (int i = 0; i < LPT; ++i) r.x[i] = kInf;
+    }
+    return r;
 }
 
 // One vertex slot: all TPV threads of a group call this with the same v.
@@ -128,13 +133,19 @@ __device__ __forceinline__ void scan_vertex(const SweepParams& p, int v, bool va
         a = __ldg(p.down_off + v);
         e = __ldg(p.down_off + v + 1);
     }
-    for (; a + 4 <= e; a += 4) {
-        const int2 a0 = __ldg(p.down_arc + a), a1 = __ldg(p.down_arc + a + 1);
-        const int2 a2 = __ldg(p.down_arc + a + 2), a3 = __ldg(p.down_arc + a + 3);
+    // four rows in flight per round, the last round predicated, so a vertex
+    // with n arcs waits for ceil(n/4) round trips; a predicated-off row is
+    // kInf with length 0 and never lowers the minimum
+    for (; a < e; a += 4) {
+        const bool o1 = a + 1 < e, o2 = a + 2 < e, o3 = a + 3 < e;
+        const int2 a0 = __ldg(p.down_arc + a);
+        const int2 a1 = o1 ? __ldg(p.down_arc + a + 1) : make_int2(0, 0);
+        const int2 a2 = o2 ? __ldg(p.down_arc + a + 2) : make_int2(0, 0);
+        const int2 a3 = o3 ? __ldg(p.down_arc + a + 3) : make_int2(0, 0);
         const Row<LPT> r0 = load_row<LPT>(p.d + (size_t)a0.x * K + sub * LPT);
-        const Row<LPT> r1 = load_row<LPT>(p.d + (size_t)a1.x * K + sub * LPT);
-        const Row<LPT> r2 = load_row<LPT>(p.d + (size_t)a2.x * K + sub * LPT);
-        const Row<LPT> r3 = load_row<LPT>(p.d + (size_t)a3.x * K + sub * LPT);
+        const Row<LPT> r1 = load_row_if<LPT>(p.d + (size_t)a1.x * K + sub * LPT, o1);
+        const Row<LPT> r2 = load_row_if<LPT>(p.d + (size_t)a2.x * K + sub * LPT, o2);
+        const Row<LPT> r3 = load_row_if<LPT>(p.d + (size_t)a3.x * K + sub * LPT, o3);
 #pragma unroll
         for (int i = 0; i < LPT; ++i) {
             const uint32_t m01 = min(r0.x[i] + (uint32_t)a0.y, r1.x[i] + (uint32_t)a1.y);
@@ -142,7 +153,6 @@ __device__ __forceinline__ void scan_vertex(const SweepParams& p, int v, bool va
             acc.x[i] = min(acc.x[i], min(m01, m23));
         }
     }
-    for (; a < e; ++a) relax<LPT>(acc, p.d, K, __ldg(p.down_arc + a), sub);
     unsigned long long bits = 0;
 #pragma unroll
     for (int i = 0; i < LPT; ++i) {

@@ -13,6 +13,8 @@
 // Work is cut into chunks of VPB consecutive vertices of one level and run in
 // the order of a host-built schedule (schedule.cpp) that interleaves levels
 // region by region for L2 reuse; schedule position q belongs to CTA q mod G.
+// (Handing positions out dynamically from a global counter was measured
+// slower: a CTA then holds positions it cannot start for a whole window.)
 // Each CTA (1024 threads, one per SM) has 31 consumer warps and one producer
 // warp, and holds up to kStages chunks at once.
 // The producer copies each chunk's CSR offsets and its contiguous block of
@@ -196,6 +198,8 @@ __device__ __forceinline__ int lane_of(int sub, int i) {
     else return sub * LPT + i;
 }
 
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 // Polling load of a completion flag.  Flags are read relaxed, so that all of a
 // pass's loads are in flight at once; the reader fences (acquire) once after
 // seeing every flag it needs set.
@@ -205,28 +209,44 @@ __device__ __forceinline__ uint32_t ld_relaxed(const int32_t* a) {
     return v;
 }
 
-// Gathers rows d[u] + len(u,v) for arcs a, a+STEP, a+2*STEP, ... < e into acc.
+// Row of a predicated gather: the label row, or all kInf when `ok` is false
+// (no memory access then).
+template <int LPT, int TPV>
+__device__ __forceinline__ Row<LPT> load_row_if(const uint32_t* row, int sub, bool ok) {
+    Row<LPT> r;
+    if (ok) {
+        r = load_row<LPT, TPV>(row, sub);
+    } else {
+#pragma unroll
+        for (int i = 0; i < LPT; ++i) r.x[i] = kInf;
+    }
+    return r;
+}
+
+// Gathers rows d[u] + len(u,v) for arcs a, a+STEP, a+2*STEP, ... < e into acc,
+// four rows in flight per round and every round four wide (the last one
+// predicated), so a vertex with n arcs waits for ceil(n/4) round trips.
+// A predicated-off row is kInf with length 0, which never lowers the minimum
+// (kInf + len cannot wrap: kInf + 0x7FFFFFFE < 2^32).
 template <int K, int LPT, int TPV, int STEP>
 __device__ __forceinline__ void gather(Row<LPT>& acc, const uint32_t* d, const int2* arcs, uint32_t a, uint32_t e,
                                        int sub) {
-    for (; a + 3 * STEP < e; a += 4 * STEP) {
-        const int2 a0 = arcs[a], a1 = arcs[a + STEP], a2 = arcs[a + 2 * STEP], a3 = arcs[a + 3 * STEP];
+    for (; a < e; a += 4 * STEP) {
+        const bool o1 = a + STEP < e, o2 = a + 2 * STEP < e, o3 = a + 3 * STEP < e;
+        const int2 a0 = arcs[a];
+        const int2 a1 = o1 ? arcs[a + STEP] : make_int2(0, 0);
+        const int2 a2 = o2 ? arcs[a + 2 * STEP] : make_int2(0, 0);
+        const int2 a3 = o3 ? arcs[a + 3 * STEP] : make_int2(0, 0);
         const Row<LPT> r0 = load_row<LPT, TPV>(d + (size_t)a0.x * K, sub);
-        const Row<LPT> r1 = load_row<LPT, TPV>(d + (size_t)a1.x * K, sub);
-        const Row<LPT> r2 = load_row<LPT, TPV>(d + (size_t)a2.x * K, sub);
-        const Row<LPT> r3 = load_row<LPT, TPV>(d + (size_t)a3.x * K, sub);
+        const Row<LPT> r1 = load_row_if<LPT, TPV>(d + (size_t)a1.x * K, sub, o1);
+        const Row<LPT> r2 = load_row_if<LPT, TPV>(d + (size_t)a2.x * K, sub, o2);
+        const Row<LPT> r3 = load_row_if<LPT, TPV>(d + (size_t)a3.x * K, sub, o3);
 #pragma unroll
         for (int i = 0; i < LPT; ++i) {
             const uint32_t m01 = min(r0.x[i] + (uint32_t)a0.y, r1.x[i] + (uint32_t)a1.y);
             const uint32_t m23 = min(r2.x[i] + (uint32_t)a2.y, r3.x[i] + (uint32_t)a3.y);
             acc.x[i] = min(acc.x[i], min(m01, m23));
         }
-    }
-    for (; a < e; a += STEP) {
-        const int2 a0 = arcs[a];
-        const Row<LPT> r0 = load_row<LPT, TPV>(d + (size_t)a0.x * K, sub);
-#pragma unroll
-        for (int i = 0; i < LPT; ++i) acc.x[i] = min(acc.x[i], r0.x[i] + (uint32_t)a0.y);
     }
 }
 
@@ -340,6 +360,25 @@ __device__ __forceinline__ void process_chunk(const SweepParams& p, const Smem& 
     else vertex_update<K, TPV, false>(p, sm, v, valid, a, e, arcs, store, tid);
 }
 
+// Bookkeeping of a polling loop that found nothing to do (lane 0 decides):
+// true once the kernel has failed elsewhere or this warp has been idle for
+// longer than the timeout (then the status records the timeout).  The clock is
+// read only while idle.
+__device__ __forceinline__ bool idle_too_long(const SweepParams& p, unsigned long long& idle_since, int lane) {
+    if (lane != 0) return false;
+    if (*(volatile int32_t*)p.status != kStOk) return true;
+    const unsigned long long now = global_ns();
+    if (idle_since == 0) {
+        idle_since = now;
+        return false;
+    }
+    if (now - idle_since > (unsigned long long)p.timeout_ns) {
+        atomicCAS(p.status, kStOk, kStTimeout);
+        return true;
+    }
+    return false;
+}
+
 // A consumer warp is done with the chunk in `stage` (schedule position q, level
 // block `level`): the last of the consumer warps to get here publishes the
 // position as complete to every CTA; each warp releases the buffer.
@@ -350,7 +389,7 @@ __device__ __forceinline__ void release_chunk(const SweepParams& p, Smem& sm, in
         if (atomicAdd(&sm.finished[stage], 1) == kConsumers / 32 - 1) {
             __threadfence_block();
             sm.finished[stage] = 0;
-            __threadfence();
+            fence_acq_rel_gpu();  // release: the CTA's rows before the flag
             *(volatile int32_t*)(p.done + q) = 1;
             if (p.trace) atomicMax((unsigned long long*)p.trace + 1 + level, global_ns());
         }
@@ -409,7 +448,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tma(SweepParams p) {
             }
             posted = 1;
         }
-        unsigned long long last_progress = global_ns();
+        // schedule record of chunk t, loaded one chunk ahead so that issuing
+        // never waits for it
+        int4 n0 = make_int4(0, 0, 0, 0), n1 = n0;
+        if (lane < kStages && t < n_mine) {
+            n0 = __ldg(p.sched_info + 2 * ((size_t)blockIdx.x + (size_t)t * G));
+            n1 = __ldg(p.sched_info + 2 * ((size_t)blockIdx.x + (size_t)t * G) + 1);
+        }
+        unsigned long long idle_since = 0;
         uint32_t nap = 32;
         while (posted < n_mine) {
             // (1) copy the next chunk into every free stage
@@ -417,8 +463,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tma(SweepParams p) {
                                (t < kStages || mbar_test_wait(&sm.empty[lane], ((uint32_t)(t / kStages) & 1u) ^ 1u));
             if (issue) {
                 const int pos = (int)blockIdx.x + t * G;
-                const int4 c0 = __ldg(p.sched_info + 2 * (size_t)pos);      // v0, v1, level, mode
-                const int4 c1 = __ldg(p.sched_info + 2 * (size_t)pos + 1);  // arc base, arcs, deps start, deps
+                const int4 c0 = n0;  // v0, v1, level, mode
+                const int4 c1 = n1;  // arc base, arcs, deps start, deps
                 const int ob = c0.x & ~3;
                 uint32_t obytes = 0, abytes = 0;
                 int big = 0;
@@ -438,6 +484,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tma(SweepParams p) {
                 cur_pa = c1.z;
                 cur_np = c1.w;
                 t += kStages;
+                if (t < n_mine) {
+                    n0 = __ldg(p.sched_info + 2 * ((size_t)blockIdx.x + (size_t)t * G));
+                    n1 = __ldg(p.sched_info + 2 * ((size_t)blockIdx.x + (size_t)t * G) + 1);
+                }
             }
             bool progress = __any_sync(0xffffffffu, issue);
             // (2) post the staged chunks whose copies have landed and whose
@@ -469,7 +519,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tma(SweepParams p) {
                 notdone = __reduce_or_sync(0xffffffffu, notdone);
                 const uint32_t now_ready = cand & ~notdone;
                 if (now_ready) {
-                    __threadfence();  // acquire: the flags seen set order the label rows behind them
+                    fence_acq_rel_gpu();  // acquire: the flags seen set order the label rows behind them
                     if ((now_ready >> lane) & 1u) {
                         *(volatile int*)&sm.ready_it[lane] = cur + 1;
                         cur = -1;
@@ -480,20 +530,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tma(SweepParams p) {
             }
             if (progress) {
                 nap = 32;
-                last_progress = global_ns();
+                idle_since = 0;
                 continue;
             }
             __nanosleep(nap);
             if (nap < 256) nap <<= 1;
-            int give_up = 0;
-            if (lane == 0) {
-                if (*(volatile int32_t*)p.status != kStOk) give_up = 1;
-                else if (global_ns() - last_progress > (unsigned long long)p.timeout_ns) {
-                    atomicCAS(p.status, kStOk, kStTimeout);
-                    give_up = 1;
-                }
-            }
-            if (__shfl_sync(0xffffffffu, give_up, 0)) break;
+            if (__shfl_sync(0xffffffffu, (int)idle_too_long(p, idle_since, lane), 0)) break;
         }
         // every issued copy must land before the CTA exits
         if (lane < kStages && t >= kStages) {
@@ -515,7 +557,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tma(SweepParams p) {
         release_chunk(p, sm, 0, 0, head.z, lane);
         base = 1;
     }
-    unsigned long long last_progress = global_ns();
+    unsigned long long idle_since = 0;
     uint32_t nap = 32;
     while (base < n_mine) {
         // lane d looks at chunk base + d of the window
@@ -530,19 +572,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tma(SweepParams p) {
         if (!ready) {
             __nanosleep(nap);
             if (nap < 256) nap <<= 1;
-            int give_up = 0;
-            if (lane == 0) {
-                if (*(volatile int32_t*)p.status != kStOk) give_up = 1;
-                else if (global_ns() - last_progress > (unsigned long long)p.timeout_ns) {
-                    atomicCAS(p.status, kStOk, kStTimeout);
-                    give_up = 1;
-                }
-            }
-            if (__shfl_sync(0xffffffffu, give_up, 0)) break;
+            if (__shfl_sync(0xffffffffu, (int)idle_too_long(p, idle_since, lane), 0)) break;
             continue;
         }
         nap = 32;
-        last_progress = global_ns();
+        idle_since = 0;
         const int pick = __ffs(ready) - 1;
         const int t = base + pick;
         const int stage = t % kStages;
