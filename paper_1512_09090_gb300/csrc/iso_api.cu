@@ -110,9 +110,12 @@ struct iso_graph {
     int2* down_arc = nullptr;
     uint32_t* up_off = nullptr;
     int2* up_arc = nullptr;
-    uint32_t* orig_off = nullptr;
-    int32_t* orig_head = nullptr;
-    int32_t* orig_id = nullptr;
+    // input arcs grouped by tail, tails in BFS order of the input graph (so
+    // that emission reads the masks of neighbouring vertices close in time)
+    uint32_t* orig_off = nullptr;   // [n+1] by emission index
+    int32_t* orig_head = nullptr;   // heads as sweep positions
+    int32_t* orig_id = nullptr;     // input arc ids
+    int32_t* emit_tail = nullptr;   // [n] sweep position of the tail at each emission index
     int32_t* perm = nullptr;
     int32_t* pos = nullptr;
     int32_t* level_off = nullptr;
@@ -121,7 +124,7 @@ struct iso_graph {
     std::vector<uint32_t> h_down_off;
     std::vector<int32_t> h_down_src, h_bfs;
     struct CachedSchedule {
-        int vpb, narrow_width, solo_levels, delay;
+        int vpb, narrow_width, sync_levels, delay;
         std::shared_ptr<SweepSchedule> s;
     };
     std::vector<CachedSchedule> schedules;
@@ -147,6 +150,7 @@ struct iso_workspace {
     int sched_delay = 0;         // TMA sweep: schedule distance to dependencies
     int solo_width = 0;          // TMA sweep: top levels up to this size run in one CTA (0: none)
     int solo_levels = 0;         // ... how many levels that is on this graph
+    int sync_levels = 0;         // TMA sweep: leading levels swept level by level before the schedule
     bool record_trace = false;
     long long* trace = nullptr;  // device [nsched + 1]
     std::vector<long long> h_trace;
@@ -185,6 +189,9 @@ struct iso_workspace {
     int k = 0;
     bool want_dist = false;
     bool submitted = false;
+    // a failed batch can stop the sweep before it clears every upward-label
+    // flag; the next batch then starts by clearing them all
+    bool stale_flags = false;
     float phase_ms[4] = {};
     cudaEvent_t ev[6] = {};
     cudaGraphExec_t gexec[2] = {};  // indexed by want_dist
@@ -242,41 +249,42 @@ int build_schedule(iso_workspace* ws) {
     if (ws->kernel == 1) {
         // TMA sweep: locality-ordered chunk schedule, cached on the graph
         const int delay = ws->sched_delay;
-        // the top levels with at most solo_width vertices each form the top block
+        // The leading levels sweep level by level before the schedule: those
+        // with at most solo_width vertices in CTA 0 alone, the following ones
+        // narrower than narrow_width in all CTAs with a grid barrier per level.
         int solo = 0;
         while (ws->solo_width > 0 && solo < g->L &&
                g->h_level_off[solo + 1] - g->h_level_off[solo] <= ws->solo_width)
             ++solo;
+        int sync = solo;
+        while (sync < g->L && g->h_level_off[sync + 1] - g->h_level_off[sync] < ws->narrow_width) ++sync;
         ws->solo_levels = solo;
+        ws->sync_levels = sync;
         static_assert(sizeof(SchedChunk) == 2 * sizeof(int4), "schedule record layout");
         std::shared_ptr<SweepSchedule> sc;
         for (auto& c : g->schedules)
-            if (c.vpb == ws->vpb && c.narrow_width == ws->narrow_width && c.solo_levels == solo && c.delay == delay)
+            if (c.vpb == ws->vpb && c.narrow_width == ws->narrow_width && c.sync_levels == sync && c.delay == delay)
                 sc = c.s;
         if (!sc) {
             sc = std::make_shared<SweepSchedule>();
             if (iso_make_schedule(g->n, g->L, g->h_level_off.data(), g->h_down_off.data(), g->h_down_src.data(),
-                                  g->h_bfs.data(), ws->vpb, 31, ws->narrow_width, solo, delay, sc.get()) != 0) {
+                                  g->h_bfs.data(), ws->vpb, 31, ws->narrow_width, sync, delay, sc.get()) != 0) {
                 iso::set_error("workspace: could not build the sweep schedule");
                 return ISO_E_INVAL;
             }
-            for (int q = 1; q < sc->Q; ++q)
-                if (sc->info[q].mode == 2) {  // the sweep runs the top block only as CTA 0's first chunk
-                    iso::set_error("workspace: top block not first in the sweep schedule");
-                    return ISO_E_INVAL;
-                }
-            g->schedules.push_back({ws->vpb, ws->narrow_width, solo, delay, sc});
+            g->schedules.push_back({ws->vpb, ws->narrow_width, sync, delay, sc});
         }
         ws->Q = sc->Q;
-        ws->sched_info = (int4*)ws->alloc((size_t)sc->Q * sizeof(SchedChunk));
+        ws->sched_info = (int4*)ws->alloc(std::max<size_t>(sc->Q, 1) * sizeof(SchedChunk));
         ws->pred = (int32_t*)ws->alloc(sc->pred.size() * 4);
-        ws->done = (int32_t*)ws->alloc((size_t)sc->Q * 4);
+        ws->done = (int32_t*)ws->alloc(std::max<size_t>(sc->Q, 1) * 4);
         if (!ws->sched_info || !ws->pred || !ws->done) {
             iso::set_error("workspace: device allocation failed");
             return ISO_E_NOMEM;
         }
-        ISO_CK(cudaMemcpyAsync(ws->sched_info, sc->info.data(), (size_t)sc->Q * sizeof(SchedChunk),
-                               cudaMemcpyHostToDevice, ws->stream));
+        if (sc->Q)
+            ISO_CK(cudaMemcpyAsync(ws->sched_info, sc->info.data(), (size_t)sc->Q * sizeof(SchedChunk),
+                                   cudaMemcpyHostToDevice, ws->stream));
         ISO_CK(cudaMemcpyAsync(ws->pred, sc->pred.data(), sc->pred.size() * 4, cudaMemcpyHostToDevice, ws->stream));
     }
     ISO_CK(cudaStreamSynchronize(ws->stream));
@@ -334,6 +342,8 @@ int enqueue(iso_workspace* ws, bool want_dist, bool capturing) {
     sw.sched_info = ws->sched_info;
     sw.pred = ws->pred;
     sw.done = ws->done;
+    sw.solo_levels = ws->solo_levels;
+    sw.sync_levels = ws->sync_levels;
     sw.Q = ws->Q;
     sw.upmask = ws->upmask;
     if (ws->kernel == 1) ISO_CK(iso_launch_sweep_tma(sw, K, ws->tpv, ws->grid, s));
@@ -342,6 +352,8 @@ int enqueue(iso_workspace* ws, bool want_dist, bool capturing) {
 
     EmitParams em{};
     em.orig_off = g->orig_off; em.orig_head = g->orig_head; em.orig_id = g->orig_id; em.mask = ws->mask;
+    em.tail_of = g->emit_tail;
+    em.status = ws->status();
     em.ecnt = ws->ecnt(); em.ebuf = ws->ebuf; em.n = g->n; em.ecap = ws->ecap;
     ISO_CK(iso_launch_emit(em, K, g->num_sms * 8, s));
     ISO_CK(record(ws->ev[3], s, capturing));
@@ -349,6 +361,7 @@ int enqueue(iso_workspace* ws, bool want_dist, bool capturing) {
     GatherParams ga{};
     ga.ebuf = ws->ebuf; ga.ecnt = ws->ecnt(); ga.tmp = ws->tmp; ga.out = ws->out; ga.out_off = ws->out_off;
     ga.k = K; ga.ecap = ws->ecap;
+    ga.status = ws->status();
     ga.key_bits = 1;
     while (ga.key_bits < 31 && (int64_t(1) << ga.key_bits) < g->m) ++ga.key_bits;
     ISO_CK(iso_launch_sort_gather(ga, K, s));
@@ -364,6 +377,11 @@ int enqueue(iso_workspace* ws, bool want_dist, bool capturing) {
 }
 
 int launch_batch(iso_workspace* ws, bool want_dist) {
+    if (ws->stale_flags) {
+        ISO_CK(cudaMemsetAsync(ws->upflag, 0, (size_t)ws->g->n, ws->stream));
+        if (ws->upmask) ISO_CK(cudaMemsetAsync(ws->upmask, 0, (size_t)ws->g->n * 8, ws->stream));
+        ws->stale_flags = false;
+    }
     if (want_dist && !ws->dist) {
         ws->dist = (int32_t*)ws->alloc((size_t)ws->K * ws->g->n * 4);
         if (!ws->dist) { iso::set_error("workspace: device allocation failed"); return ISO_E_NOMEM; }
@@ -462,10 +480,28 @@ extern "C" int iso_upload_graph(const iso_ch* ch, const iso_alloc* alloc, void* 
         free_all(); return rc;
     }
     ISO_CK(cudaStreamSynchronize(g->stream));
-    for (size_t i = 0; i <= n; ++i) off32[i] = (uint32_t)ch->orig_off[i];
+    std::vector<int32_t> tail(n), head, aid;
+    try {
+        head.resize(ch->orig_head.size());
+        aid.resize(ch->orig_id.size());
+    } catch (const std::bad_alloc&) {
+        free_all();
+        iso::set_error("iso_upload_graph: out of host memory");
+        return ISO_E_NOMEM;
+    }
+    for (size_t v = 0; v < n; ++v) tail[(size_t)ch->bfs[v]] = (int32_t)v;
+    off32[0] = 0;
+    for (size_t i = 0; i < n; ++i) {
+        const int32_t v = tail[i];
+        const int64_t a = ch->orig_off[v], b = ch->orig_off[v + 1];
+        std::copy(ch->orig_head.begin() + a, ch->orig_head.begin() + b, head.begin() + off32[i]);
+        std::copy(ch->orig_id.begin() + a, ch->orig_id.begin() + b, aid.begin() + off32[i]);
+        off32[i + 1] = off32[i] + (uint32_t)(b - a);
+    }
     if ((rc = g->upload(&g->orig_off, off32.data(), n + 1)) ||
-        (rc = g->upload(&g->orig_head, ch->orig_head.data(), ch->orig_head.size())) ||
-        (rc = g->upload(&g->orig_id, ch->orig_id.data(), ch->orig_id.size())) ||
+        (rc = g->upload(&g->orig_head, head.data(), head.size())) ||
+        (rc = g->upload(&g->orig_id, aid.data(), aid.size())) ||
+        (rc = g->upload(&g->emit_tail, tail.data(), n)) ||
         (rc = g->upload(&g->perm, ch->perm.data(), n)) || (rc = g->upload(&g->pos, ch->pos.data(), n)) ||
         (rc = g->upload(&g->level_off, ch->level_off.data(), ch->level_off.size()))) {
         free_all(); return rc;
@@ -629,6 +665,7 @@ int collect_impl(iso_workspace* ws, int64_t* out_offsets, int32_t* out_arcs, int
     for (int attempt = 0;; ++attempt) {
         ISO_CK(cudaEventSynchronize(ws->ev[5]));
         const int st = ws->h_ctl[0];
+        if (st != kStOk) ws->stale_flags = true;
         if (st == kStTimeout) { ws->submitted = false; iso::set_error("sweep: a grid barrier timed out"); return ISO_E_TIMEOUT; }
         if (st == kStBadInput) { ws->submitted = false; iso::set_error("query: a source or limit failed validation"); return ISO_E_INVAL; }
         int grow_up = st == kStUpOverflow;
@@ -794,7 +831,7 @@ struct iso_graph_view {
     int64_t m;
     const uint32_t *down_off, *up_off, *orig_off;
     const int2 *down_arc, *up_arc;
-    const int32_t *orig_head, *orig_id, *pos, *level_off;
+    const int32_t *orig_head, *orig_id, *pos, *level_off, *emit_tail;
     const int32_t* h_level_off;
 };
 
@@ -804,6 +841,7 @@ int iso_graph_view_of(const iso_graph* g, iso_graph_view* v) {
     v->down_off = g->down_off; v->up_off = g->up_off; v->orig_off = g->orig_off;
     v->down_arc = g->down_arc; v->up_arc = g->up_arc;
     v->orig_head = g->orig_head; v->orig_id = g->orig_id; v->pos = g->pos; v->level_off = g->level_off;
+    v->emit_tail = g->emit_tail;
     v->h_level_off = g->h_level_off.data();
     return ISO_OK;
 }

@@ -76,14 +76,18 @@ struct SweepParams {
                                //      {first staged arc, arcs, dependency list start, its length}
     const int32_t* pred;       // dependency lists (positions), each 16-byte aligned
     int32_t* done;             // [Q] 1 once a position is complete; zeroed per batch
+    int solo_levels;           // TMA kernel: levels 0 .. solo_levels-1 are swept by CTA 0 alone,
+    int sync_levels;           // then levels .. sync_levels-1 by all CTAs, a grid barrier per level
     int Q;
     unsigned long long* upmask;// [n] lanes with an upward label (TMA kernel)
 };
 
 struct EmitParams {
-    const uint32_t* orig_off;  // [n+1]
+    const uint32_t* orig_off;  // [n+1] input arcs grouped by tail, by emission index
     const int32_t* orig_head;  // sweep positions
     const int32_t* orig_id;
+    const int32_t* tail_of;    // [n] sweep position of the tail at each emission index
+    const int32_t* status;     // batch status: emission is skipped once it is not kStOk
     const void* mask;
     int32_t* ecnt;             // [K]
     int32_t* ebuf;             // [K * ecap]
@@ -98,6 +102,7 @@ struct GatherParams {
     int64_t* out_off;          // [K+1]
     int k, ecap;
     int key_bits;              // bits needed for arc ids
+    const int32_t* status;     // batch status: nothing is written once it is not kStOk
 };
 
 struct DistParams {

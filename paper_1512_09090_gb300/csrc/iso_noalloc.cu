@@ -91,7 +91,7 @@ struct iso_graph_view {
     int64_t m;
     const uint32_t *down_off, *up_off, *orig_off;
     const int2 *down_arc, *up_arc;
-    const int32_t *orig_head, *orig_id, *pos, *level_off;
+    const int32_t *orig_head, *orig_id, *pos, *level_off, *emit_tail;
     const int32_t* h_level_off;
 };
 int iso_graph_view_of(const iso_graph* g, iso_graph_view* v);
@@ -187,12 +187,15 @@ extern "C" int iso_query_noalloc(iso_graph* g, int32_t k, const int32_t* sources
 
     EmitParams em{};
     em.orig_off = gv.orig_off; em.orig_head = gv.orig_head; em.orig_id = gv.orig_id; em.mask = sw.mask;
+    em.tail_of = gv.emit_tail;
+    em.status = ctl;
     em.ecnt = ctl + 8; em.ebuf = (int32_t*)(base + kOffEbuf); em.n = gv.n; em.ecap = kMaxArcs;
     if ((e = iso_launch_emit(em, kLanes, gv.num_sms * 8, stream)) != cudaSuccess)
         return fail(ISO_E_CUDA, "emit launch", e);
     GatherParams ga{};
     ga.ebuf = em.ebuf; ga.ecnt = em.ecnt; ga.tmp = (int32_t*)(base + kOffTmp); ga.out = (int32_t*)(base + kOffOut);
     ga.out_off = (int64_t*)(base + kOffOutOff); ga.k = kLanes; ga.ecap = kMaxArcs;
+    ga.status = ctl;
     ga.key_bits = 1;
     while (ga.key_bits < 31 && (int64_t(1) << ga.key_bits) < gv.m) ++ga.key_bits;
     if ((e = iso_launch_sort_gather(ga, kLanes, stream)) != cudaSuccess)

@@ -1,8 +1,9 @@
 // Isochrone edge emission (Section 3): arc (u,v) of the input graph is an
 // isochrone edge for lane i iff exactly one of u, v is in range, i.e. iff bit i
-// of mask[u] XOR mask[v] is set.  Arcs are visited grouped by tail (sweep
-// order), so mask[u] is read once per vertex and mask[v] is a gather from a
-// small array the sweep just wrote.  Per lane, ids are appended with one
+// of mask[u] XOR mask[v] is set.  Arcs are visited grouped by tail, tails in
+// BFS order of the input graph: neighbouring warps then read the masks of
+// neighbouring vertices, which sit in a few short stretches of each level's
+// part of the mask array and stay in L2, instead of scattered sectors.  Per lane, ids are appended with one
 // atomicAdd per warp: __ballot_sync gives the warp's members for that lane and
 // __popc of the lower lanes gives each member's slot.
 //
@@ -33,18 +34,25 @@ __device__ __forceinline__ unsigned long long warp_or(unsigned long long x) {
 template <int K>
 __global__ void __launch_bounds__(kEmitThreads) k_emit(EmitParams p) {
     using MaskT = typename MaskOf<K>::T;
+    // bits of lanes that exist: a mask word holds at least 8 bits, and after a
+    // failed sweep it may hold anything
+    constexpr unsigned long long kLanes = K >= 64 ? ~0ull : ((1ull << K) - 1ull);
+    // a failed batch (bad input, upward overflow, timeout) is reported by the
+    // host; its masks may be stale, so nothing is emitted
+    if (*(volatile const int32_t*)p.status != kStOk) return;
     const MaskT* mask = static_cast<const MaskT*>(p.mask);
     const unsigned lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int warps = (int)(gridDim.x * blockDim.x) >> 5;
-    // a warp takes 32 consecutive tails; their arcs are one contiguous range
+    // a warp takes 32 consecutive tails (emission indices); their arcs are one
+    // contiguous range
     for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); w * 32 < p.n; w += warps) {
         const int u0 = w * 32;
         const int u = min(u0 + (int)lane, p.n);
         const uint32_t my_off = __ldg(p.orig_off + u);           // start of tail u0+lane's arcs
         const uint32_t a0 = __shfl_sync(0xffffffffu, my_off, 0);
         const uint32_t a1 = __ldg(p.orig_off + min(u0 + 32, p.n));
-        const unsigned long long mu_lane = u < p.n ? (unsigned long long)mask[u] : 0ull;
+        const unsigned long long mu_lane = u < p.n ? (unsigned long long)mask[__ldg(p.tail_of + u)] : 0ull;
         for (uint32_t base = a0; base < a1; base += 32) {
             const uint32_t a = base + lane;
             unsigned long long x = 0;
@@ -58,7 +66,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(EmitParams p) {
             }
             const unsigned long long mu = __shfl_sync(0xffffffffu, mu_lane, lo);
             if (a < a1) {
-                x = mu ^ (unsigned long long)mask[__ldg(p.orig_head + a)];
+                x = (mu ^ (unsigned long long)mask[__ldg(p.orig_head + a)]) & kLanes;
                 if (x) id = __ldg(p.orig_id + a);
             }
             if (!__any_sync(0xffffffffu, x != 0)) continue;
@@ -113,6 +121,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_gather(GatherParams p) {
     __shared__ long long s_off;
     __shared__ int s_nbig, s_big[256];
     const int lane = blockIdx.x;
+    if (*(volatile const int32_t*)p.status != kStOk) return;  // failed batch: the host reports it
     if (threadIdx.x == 0) {
         long long off = 0;
         for (int i = 0; i < lane; ++i) off += min(p.ecnt[i], p.ecap);

@@ -57,8 +57,7 @@ template <> struct MaskOf<64> { using T = unsigned long long; };
 struct Meta {
     int v0, v1;   // vertices [v0, v1)
     int abase;    // first arc index held in the stage buffer
-    int flags;    // bit 0: arcs did not fit (read them from global memory); bits 1-2: mode
-                  // (0 a thread group per vertex, 1 a warp per vertex, 2 the top block)
+    int flags;    // bit 0: arcs did not fit (read them from global memory); bit 1: a warp per vertex
     int q, level; // schedule position and level block
     int pad[2];
 };
@@ -324,21 +323,84 @@ __device__ __forceinline__ void vertex_update(const SweepParams& p, const Smem& 
     if (valid && sub == 0 && g == 0) static_cast<MaskT*>(p.mask)[v] = (MaskT)bits;
 }
 
-// The top block (levels 0..last), swept level by level by all consumer warps
-// of CTA 0 together, with a named barrier after each level.  They run it first
-// thing, unconditionally: it needs no staged data and depends on nothing, so
-// every consumer warp reaches every barrier.
+// Levels lo_level .. hi_level-1, swept by this CTA alone (all 32 warps), a
+// warp per vertex, with a CTA barrier after each level.
 template <int K, int TPV>
-__device__ void process_top_block(const SweepParams& p, const Smem& sm, int last, int warp, int tid) {
-    for (int j = 0; j <= last; ++j) {
+__device__ void sweep_levels_cta(const SweepParams& p, const Smem& sm, int lo_level, int hi_level, int warp, int tid) {
+    for (int j = lo_level; j < hi_level; ++j) {
         const int lo = __ldg(p.level_off + j), hi = __ldg(p.level_off + j + 1);
         const bool store = p.write_all || j != p.last_level_block;
-        for (int v = lo + warp; v < hi; v += kConsumers / 32)
+        for (int v = lo + warp; v < hi; v += kThreads / 32)
             vertex_update<K, TPV, true>(p, sm, v, true, __ldg(p.down_off + v), __ldg(p.down_off + v + 1), p.down_arc,
                                         store, tid);
-        asm volatile("bar.sync 1, 992;" ::: "memory");
+        __syncthreads();
         if (p.trace && tid == 0) atomicMax((unsigned long long*)p.trace + 1 + j, global_ns());
     }
+}
+
+// Level j, swept by all CTAs together: a warp per vertex if the level has no
+// more vertices than the grid has warps, else a group of TPV threads per vertex.
+template <int K, int TPV>
+__device__ void sweep_level_grid(const SweepParams& p, const Smem& sm, int j, int warp, int tid) {
+    const int lo = __ldg(p.level_off + j), hi = __ldg(p.level_off + j + 1);
+    const bool store = p.write_all || j != p.last_level_block;
+    const int warps = (int)gridDim.x * (kThreads / 32);
+    if (hi - lo <= warps) {
+        const int v = lo + (int)blockIdx.x * (kThreads / 32) + warp;
+        if (v < hi)  // warp-uniform
+            vertex_update<K, TPV, true>(p, sm, v, true, __ldg(p.down_off + v), __ldg(p.down_off + v + 1), p.down_arc,
+                                        store, tid);
+    } else {
+        const int groups = (int)gridDim.x * (kThreads / TPV);
+        for (int b = lo; b < hi; b += groups) {  // uniform bounds: every thread takes part in the shuffles
+            const int v = b + (int)blockIdx.x * (kThreads / TPV) + tid / TPV;
+            const bool valid = v < hi;
+            vertex_update<K, TPV, false>(p, sm, v, valid, valid ? __ldg(p.down_off + v) : 0u,
+                                         valid ? __ldg(p.down_off + v + 1) : 0u, p.down_arc, store, tid);
+        }
+    }
+}
+
+// Grid-wide barrier of the whole CTA (the launch is cooperative, so every CTA
+// is resident).  Bounded: gives up, recording kStTimeout, after the timeout
+// (bar_extra adds arrivals that never come, for the tests).  Returns false,
+// the same on every thread of the CTA, if the kernel has failed.
+__device__ bool grid_sync(const SweepParams& p) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile int32_t* st = p.status;
+        volatile uint32_t* gen = p.bar + 1;
+        if (*st != kStOk) {
+            ok = 0;
+        } else {
+            const uint32_t g0 = *gen;
+            fence_acq_rel_gpu();
+            const uint32_t want = gridDim.x + (uint32_t)p.bar_extra;
+            if (atomicAdd(p.bar, 1u) + 1u == want) {
+                atomicExch(p.bar, 0u);
+                fence_acq_rel_gpu();
+                atomicAdd(p.bar + 1, 1u);
+            } else {
+                const unsigned long long t0 = global_ns();
+                for (uint32_t it = 0; *gen == g0; ++it) {
+                    if ((it & 15) == 15) {
+                        if (*st != kStOk) { ok = 0; break; }
+                        if (global_ns() - t0 > (unsigned long long)p.timeout_ns || it > (1u << 28)) {
+                            atomicCAS(p.status, kStOk, kStTimeout);
+                            ok = 0;
+                            break;
+                        }
+                    }
+                }
+            }
+            fence_acq_rel_gpu();
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
 }
 
 // The chunk held in `stage`, by one consumer warp (its share of the vertices).
@@ -408,10 +470,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tma(SweepParams p) {
     // chunks of this CTA: positions blockIdx.x, blockIdx.x + G, ...
     const int G = (int)gridDim.x;
     const int n_mine = (int)blockIdx.x < p.Q ? (p.Q - (int)blockIdx.x + G - 1) / G : 0;
-    // position 0 may be the top block (mode 2); it is CTA 0's chunk 0 and is
-    // never staged: stage 0 starts with chunk kStages, one phase later
-    const int4 head = p.Q > 0 ? __ldg(p.sched_info) : make_int4(0, 0, 0, 0);
-    const bool top = blockIdx.x == 0 && p.Q > 0 && head.w == 2;
 
     if (tid == 0) {
         for (int i = 0; i < kStages; ++i) {
@@ -429,6 +487,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tma(SweepParams p) {
     if (p.trace && tid == 0 && blockIdx.x == 0) p.trace[0] = p.trace[p.L + 1] = (long long)global_ns();
     __syncthreads();
 
+    // ---------------- the leading levels, level by level ----------------
+    // The top of the hierarchy is a long chain of small levels: CTA 0 sweeps
+    // the smallest alone (a CTA barrier per level), then all CTAs sweep the
+    // other narrow ones (a grid barrier per level).  The schedule holds no
+    // chunks of these levels and no dependencies on them.
+    if (p.sync_levels > 0) {
+        bool ok = true;
+        if (p.solo_levels > 0) {
+            if (blockIdx.x == 0) sweep_levels_cta<K, TPV>(p, sm, 0, p.solo_levels, warp, tid);
+            ok = grid_sync(p);
+        }
+        for (int j = p.solo_levels; ok && j < p.sync_levels; ++j) {
+            sweep_level_grid<K, TPV>(p, sm, j, warp, tid);
+            ok = grid_sync(p);
+            if (ok && p.trace && tid == 0 && blockIdx.x == 0) atomicMax((unsigned long long*)p.trace + 1 + j, global_ns());
+        }
+        if (!ok) return;  // the same in every thread of the CTA
+    }
+
     if (warp == kConsumers / 32) {
         // ---------------- producer warp ----------------
         // Lane s < kStages runs stage s, whose chunks are s, s + kStages, ...:
@@ -441,13 +518,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tma(SweepParams p) {
         int cur_pa = 0, cur_np = 0;
         bool cur_held = false;    // its dependency list was copied to shared memory
         int posted = 0;
-        if (top) {
-            if (lane == 0) {
-                mbar_arrive(&sm.full[0]);  // phase 0 of stage 0 stands for the top block
-                t = kStages;
-            }
-            posted = 1;
-        }
         // schedule record of chunk t, loaded one chunk ahead so that issuing
         // never waits for it
         int4 n0 = make_int4(0, 0, 0, 0), n1 = n0;
@@ -466,16 +536,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tma(SweepParams p) {
                 const int4 c0 = n0;  // v0, v1, level, mode
                 const int4 c1 = n1;  // arc base, arcs, deps start, deps
                 const int ob = c0.x & ~3;
-                uint32_t obytes = 0, abytes = 0;
-                int big = 0;
-                if (c0.w != 2) {
-                    obytes = (uint32_t)(((c0.y + 1 - ob) * 4 + 15) & ~15);
-                    big = c1.y > kArcCap;
-                    abytes = big ? 0u : (uint32_t)((c1.y * 8 + 15) & ~15);
-                }
+                const uint32_t obytes = (uint32_t)(((c0.y + 1 - ob) * 4 + 15) & ~15);
+                const int big = c1.y > kArcCap;
+                const uint32_t abytes = big ? 0u : (uint32_t)((c1.y * 8 + 15) & ~15);
                 cur_held = c1.w <= kPredCap && p.bar_extra == 0;
                 const uint32_t pbytes = cur_held ? (uint32_t)(((c1.w + 3) & ~3) * 4) : 0u;
-                sm.meta[lane] = Meta{c0.x, c0.y, c1.x, big | (c0.w << 1), pos, c0.z, {0, 0}};
+                sm.meta[lane] = Meta{c0.x, c0.y, c1.x, big | (c0.w ? 2 : 0), pos, c0.z, {0, 0}};
                 mbar_expect_tx(&sm.full[lane], obytes + abytes + pbytes);
                 if (obytes) bulk_load(sm.offs[lane], p.down_off + ob, obytes, &sm.full[lane]);
                 if (abytes) bulk_load(sm.arcs[lane], p.down_arc + c1.x, abytes, &sm.full[lane]);
@@ -552,11 +618,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tma(SweepParams p) {
     // releases the buffer; the last warp to finish a chunk publishes it.
     int base = 0;            // oldest chunk this warp has not done
     uint32_t done_bits = 0;  // bit d: chunk base + d done by this warp
-    if (top) {
-        process_top_block<K, TPV>(p, sm, head.z, warp, tid);
-        release_chunk(p, sm, 0, 0, head.z, lane);
-        base = 1;
-    }
     unsigned long long idle_since = 0;
     uint32_t nap = 32;
     while (base < n_mine) {

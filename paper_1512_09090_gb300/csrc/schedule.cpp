@@ -15,8 +15,9 @@
 //
 // The top levels of the hierarchy hold few vertices each but form a long chain
 // of dependencies; run as separate chunks, every level would cost a round trip
-// between CTAs.  The first `solo_levels` levels are therefore one chunk, which
-// a single CTA sweeps level by level with CTA barriers; it is scheduled first.
+// between CTAs.  The first `sync_levels` levels therefore get no chunks: the
+// sweep runs them level by level before it starts on the schedule, and arcs
+// from them are no dependencies.
 //
 // For position q the device receives its chunk's vertex and arc ranges and the
 // list of positions q depends on; it starts chunk q once all of them are
@@ -30,17 +31,13 @@
 #include "sweep_schedule.h"
 
 int iso_make_schedule(int n, int L, const int32_t* level_off, const uint32_t* down_off, const int32_t* down_src,
-                      const int32_t* bfs, int vpb, int narrow_chunk, int narrow_width, int solo_levels, int delay,
+                      const int32_t* bfs, int vpb, int narrow_chunk, int narrow_width, int sync_levels, int delay,
                       SweepSchedule* out) {
-    if (n <= 0 || L <= 0 || vpb <= 0 || narrow_chunk <= 0 || solo_levels < 0 || solo_levels > L) return -1;
+    if (n <= 0 || L <= 0 || vpb <= 0 || narrow_chunk <= 0 || sync_levels < 0 || sync_levels > L) return -1;
     // chunks in level order
     std::vector<int32_t> cv0, cv1, clev, cmode;
-    std::vector<int32_t> chunk_of(n);
-    if (solo_levels > 0) {
-        cv0.push_back(0); cv1.push_back(level_off[solo_levels]); clev.push_back(solo_levels - 1); cmode.push_back(2);
-        for (int v = 0; v < level_off[solo_levels]; ++v) chunk_of[v] = 0;
-    }
-    for (int j = solo_levels; j < L; ++j) {
+    std::vector<int32_t> chunk_of(n, -1);  // -1: swept before the schedule
+    for (int j = sync_levels; j < L; ++j) {
         const int lo = level_off[j], hi = level_off[j + 1];
         const int mode = narrow_width > 0 && hi - lo < narrow_width ? 1 : 0;
         const int per = mode ? narrow_chunk : vpb;
@@ -66,7 +63,7 @@ int iso_make_schedule(int n, int L, const int32_t* level_off, const uint32_t* do
             for (int v = cv0[c]; v < cv1[c]; ++v)
                 for (uint32_t a = down_off[v]; a < down_off[v + 1]; ++a) {
                     const int pc = chunk_of[down_src[a]];
-                    if (pc == c || mark[pc] == c) continue;  // arcs inside the top block
+                    if (pc < 0 || mark[pc] == c) continue;  // done before the schedule, or seen
                     mark[pc] = c;
                     if (pass == 0) { soff[pc + 1]++; indeg[c]++; }
                     else out->succ[fill[pc]++] = c;
@@ -82,7 +79,7 @@ int iso_make_schedule(int n, int L, const int32_t* level_off, const uint32_t* do
     std::vector<int64_t> earliest(Q, 0);
     std::vector<int32_t> pos_of(Q, -1);
     // spatial key, then higher level first
-    auto key = [&](int c) { return cmode[c] == 2 ? (int64_t)-1 : (int64_t)bfs[cv0[c]] * (L + 1) + clev[c]; };
+    auto key = [&](int c) { return (int64_t)bfs[cv0[c]] * (L + 1) + clev[c]; };
     for (int c = 0; c < Q; ++c)
         if (indeg[c] == 0) ready.push({key(c), c});
     out->info.resize(Q);
@@ -99,12 +96,8 @@ int iso_make_schedule(int n, int L, const int32_t* level_off, const uint32_t* do
         const int c = ready.top().second;
         ready.pop();
         pos_of[c] = q;
-        out->info[q] = {cv0[c], cv1[c], clev[c], cmode[c], 0, 0, 0, 0};
-        if (cmode[c] != 2) {
-            const uint32_t ab = down_off[cv0[c]] & ~1u;
-            out->info[q].abase = (int32_t)ab;
-            out->info[q].na = (int32_t)(down_off[cv1[c]] - ab);
-        }
+        const uint32_t ab = down_off[cv0[c]] & ~1u;
+        out->info[q] = {cv0[c], cv1[c], clev[c], cmode[c], (int32_t)ab, (int32_t)(down_off[cv1[c]] - ab), 0, 0};
         for (int32_t i = soff[c]; i < soff[c + 1]; ++i) {
             const int s = out->succ[i];
             earliest[s] = std::max<int64_t>(earliest[s], (int64_t)q + delay);

@@ -8,11 +8,10 @@
 // one 32-byte record (two int4 on the device).
 struct SchedChunk {
     int32_t v0, v1;  // sweep positions [v0, v1)
-    int32_t level;   // level block index (0 = top level); for the top block, its last level
-    int32_t mode;    // 0: a thread group per vertex, 1: a warp per vertex,
-                     // 2: the top block (levels 0..level, one CTA, level by level)
+    int32_t level;   // level block index (0 = top level)
+    int32_t mode;    // 0: a thread group per vertex, 1: a warp per vertex
     int32_t abase;   // first downward arc to stage (even, so the copy starts 16-byte aligned)
-    int32_t na;      // arcs to stage from abase (0 for the top block)
+    int32_t na;      // arcs to stage from abase
     int32_t pa;      // its dependency list: pred[pa .. pa + np), pa a multiple of 4
     int32_t np;
 };
@@ -27,9 +26,9 @@ struct SweepSchedule {
 };
 
 // Builds the schedule for chunks of `vpb` vertices (levels narrower than
-// narrow_width: chunks of narrow_chunk vertices, a warp per vertex; the first
-// solo_levels levels: one chunk run by one CTA).  Returns 0, or -1 if the
-// input is inconsistent.
+// narrow_width: chunks of narrow_chunk vertices, a warp per vertex) of levels
+// sync_levels .. L-1; the levels above are swept before the schedule starts.
+// Returns 0, or -1 if the input is inconsistent.
 int iso_make_schedule(int n, int L, const int32_t* level_off, const uint32_t* down_off, const int32_t* down_src,
-                      const int32_t* bfs, int vpb, int narrow_chunk, int narrow_width, int solo_levels, int delay,
+                      const int32_t* bfs, int vpb, int narrow_chunk, int narrow_width, int sync_levels, int delay,
                       SweepSchedule* out);

@@ -128,11 +128,21 @@ def test_fusion_and_cuda_graph(fuse, graph, kernel):
 @pytest.mark.parametrize("solo", [-1, 1, 124, 1 << 30])
 @pytest.mark.parametrize("graph", [0, 1])
 def test_top_block_sizes(solo, graph):
-    # -1: no top block; 1 << 30: the whole hierarchy is one block run by CTA 0
+    # -1: no levels in CTA 0 alone; 1 << 30: CTA 0 sweeps the whole hierarchy
     g, dg = dev_graph("grid64")
     srcs = synth.draw_sources(g, 16, 15)
     taus = synth.draw_taus_uniform(16, 0, 3000, 16)
     check_batch(g, dg, srcs, taus, solo_width=solo, use_cuda_graph=graph, sweep_kernel=1)
+
+
+@pytest.mark.parametrize("solo,fuse", [(-1, -1), (124, -1), (-1, 0), (1 << 30, 0)])
+def test_leading_level_phases(solo, fuse):
+    # fuse -1: no level-synchronous phase (every level in the chunk schedule);
+    # solo -1 with the default fuse width: all narrow levels under grid barriers
+    g, dg = dev_graph("grid1k")
+    srcs = synth.draw_sources(g, 16, 61)
+    taus = synth.draw_taus_uniform(16, 0, 60000, 62)
+    check_batch(g, dg, srcs, taus, want_dist=True, solo_width=solo, fuse_width=fuse, sweep_kernel=1)
 
 
 @pytest.mark.parametrize("solo", [-1, 124, 4000])
@@ -202,6 +212,30 @@ def test_overflow_reports_needed_offsets():
         P.iso_query(dg, srcs, taus, out_offsets=off, out_arcs=small, cap=3)
     assert e.value.code == P.ISO_E_OVERFLOW
     assert np.array_equal(off, want_off)
+
+
+@pytest.mark.parametrize("k", [1, 8, 64])
+def test_failed_batch_leaves_workspace_clean(k):
+    # one invalid source in device memory: the batch fails on the device after
+    # the other lanes' upward searches ran; the next batch on the same
+    # workspace must not see anything of it
+    g, dg = dev_graph("grid1k")
+    ws = P.Workspace(dg, k, use_cuda_graph=1)
+    srcs = synth.draw_sources(g, k, 91)
+    bad = srcs.copy()
+    bad[k // 2] = g.n + 3
+    taus = synth.draw_taus_uniform(k, 2000, 60000, 92)
+    ws.submit(torch.from_numpy(bad).cuda(), torch.from_numpy(taus).cuda())
+    with pytest.raises(P.IsoError) as e:
+        ws.collect()
+    assert e.value.code == P.ISO_E_INVAL
+    for seed in (93, 94):
+        s2 = synth.draw_sources(g, k, seed)
+        ws.submit(s2, taus)
+        off, arcs, _ = ws.collect()
+        o_off, o_arcs, _ = oracle.query_batch(g.n, g.tail, g.head, g.weight, s2, taus, threads=8)
+        assert np.array_equal(off, o_off) and np.array_equal(arcs, o_arcs)
+    ws.free()
 
 
 def test_argument_errors_and_recovery():
