@@ -42,12 +42,13 @@ namespace {
 
 using namespace isod;
 
-constexpr int kThreads = 1024;
-constexpr int kConsumers = 992;          // warps 0..30; warp 31 produces
-constexpr int kStages = 6;               // chunks a CTA holds at once; warps take any ready one
+constexpr int kThreads = 1024;           // per CTA; 1024 / kThreads CTAs per SM
+constexpr int kConsumers = kThreads - 32;  // all warps but the last consume; the last produces
+constexpr int kStages = 3;               // chunks a CTA holds at once; warps take any ready one
 constexpr int kArcCap = 1536;            // arcs per stage buffer (larger chunks read arcs from HBM)
 constexpr int kOffCap = 1024;            // offsets per stage buffer (>= VPB + 5)
 constexpr int kPredCap = 128;            // dependency list held per stage (longer lists stay in HBM)
+constexpr int kRounds = 1;               // vertices per thread group in a chunk of a wide level
 
 template <int K> struct MaskOf { using T = uint8_t; };
 template <> struct MaskOf<16> { using T = uint16_t; };
@@ -227,27 +228,45 @@ __device__ __forceinline__ Row<LPT> load_row_if(const uint32_t* row, int sub, bo
 // predicated), so a vertex with n arcs waits for ceil(n/4) round trips.
 // A predicated-off row is kInf with length 0, which never lowers the minimum
 // (kInf + len cannot wrap: kInf + 0x7FFFFFFE < 2^32).
+// One round: rows of arcs q[0..3] (q[i] taken only if on[i]; q[0] always).
+template <int K, int LPT, int TPV>
+__device__ __forceinline__ void gather_round(Row<LPT>& acc, const uint32_t* d, const int2 (&q)[4], bool o1, bool o2,
+                                             bool o3, int sub) {
+    const Row<LPT> r0 = load_row<LPT, TPV>(d + (size_t)q[0].x * K, sub);
+    const Row<LPT> r1 = load_row_if<LPT, TPV>(d + (size_t)q[1].x * K, sub, o1);
+    const Row<LPT> r2 = load_row_if<LPT, TPV>(d + (size_t)q[2].x * K, sub, o2);
+    const Row<LPT> r3 = load_row_if<LPT, TPV>(d + (size_t)q[3].x * K, sub, o3);
+#pragma unroll
+    for (int i = 0; i < LPT; ++i) {
+        const uint32_t m01 = min(r0.x[i] + (uint32_t)q[0].y, r1.x[i] + (uint32_t)q[1].y);
+        const uint32_t m23 = min(r2.x[i] + (uint32_t)q[2].y, r3.x[i] + (uint32_t)q[3].y);
+        acc.x[i] = min(acc.x[i], min(m01, m23));
+    }
+}
+
+// The arcs a, a+STEP, a+2*STEP, a+3*STEP (those below e; zero beyond).
+template <int STEP>
+__device__ __forceinline__ void arcs_of_round(int2 (&q)[4], const int2* arcs, uint32_t a, uint32_t e) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) q[r] = a + r * STEP < e ? arcs[a + r * STEP] : make_int2(0, 0);
+}
+
 template <int K, int LPT, int TPV, int STEP>
 __device__ __forceinline__ void gather(Row<LPT>& acc, const uint32_t* d, const int2* arcs, uint32_t a, uint32_t e,
                                        int sub) {
     for (; a < e; a += 4 * STEP) {
-        const bool o1 = a + STEP < e, o2 = a + 2 * STEP < e, o3 = a + 3 * STEP < e;
-        const int2 a0 = arcs[a];
-        const int2 a1 = o1 ? arcs[a + STEP] : make_int2(0, 0);
-        const int2 a2 = o2 ? arcs[a + 2 * STEP] : make_int2(0, 0);
-        const int2 a3 = o3 ? arcs[a + 3 * STEP] : make_int2(0, 0);
-        const Row<LPT> r0 = load_row<LPT, TPV>(d + (size_t)a0.x * K, sub);
-        const Row<LPT> r1 = load_row_if<LPT, TPV>(d + (size_t)a1.x * K, sub, o1);
-        const Row<LPT> r2 = load_row_if<LPT, TPV>(d + (size_t)a2.x * K, sub, o2);
-        const Row<LPT> r3 = load_row_if<LPT, TPV>(d + (size_t)a3.x * K, sub, o3);
-#pragma unroll
-        for (int i = 0; i < LPT; ++i) {
-            const uint32_t m01 = min(r0.x[i] + (uint32_t)a0.y, r1.x[i] + (uint32_t)a1.y);
-            const uint32_t m23 = min(r2.x[i] + (uint32_t)a2.y, r3.x[i] + (uint32_t)a3.y);
-            acc.x[i] = min(acc.x[i], min(m01, m23));
-        }
+        int2 q[4];
+        arcs_of_round<STEP>(q, arcs, a, e);
+        gather_round<K, LPT, TPV>(acc, d, q, a + STEP < e, a + 2 * STEP < e, a + 3 * STEP < e, sub);
     }
 }
+
+// A vertex's first round of arcs, read ahead (before a barrier) by the
+// level-synchronous sweep of narrow levels.
+struct FirstRound {
+    bool on;      // q holds the arcs of the first round
+    int2 q[4];
+};
 
 // True (on every lane) if every position in pred[pa .. pa+np) is complete right
 // now (plus bar_extra flags that never come when a test asks for a timeout).
@@ -269,7 +288,8 @@ __device__ bool deps_done_now(const SweepParams& p, int pa, int np, int lane) {
 // vertex's own state is read before the gathers instead of after them.
 template <int K, int TPV, bool WPV>
 __device__ __forceinline__ void vertex_update(const SweepParams& p, const Smem& sm, int v, bool valid, uint32_t a,
-                                              uint32_t e, const int2* arcs, bool store, int tid) {
+                                              uint32_t e, const int2* arcs, bool store, int tid,
+                                              const FirstRound& pre = FirstRound{false, {}}) {
     constexpr int LPT = K / TPV;
     constexpr int GPV = 32 / TPV;
     using MaskT = typename MaskOf<K>::T;
@@ -288,7 +308,14 @@ __device__ __forceinline__ void vertex_update(const SweepParams& p, const Smem& 
             um = __ldcg(p.upmask + v);
             prefetch_l1(p.d + (size_t)v * K, K * 4);
         }
-        if (valid) gather<K, LPT, TPV, GPV>(acc, p.d, arcs, a + g, e, sub);
+        if (valid) {
+            uint32_t b = a + g;
+            if (pre.on) {  // pre holds the arcs of this thread's group
+                if (b < e) gather_round<K, LPT, TPV>(acc, p.d, pre.q, b + GPV < e, b + 2 * GPV < e, b + 3 * GPV < e, sub);
+                b += 4 * GPV;
+            }
+            gather<K, LPT, TPV, GPV>(acc, p.d, arcs, b, e, sub);
+        }
 #pragma unroll
         for (int o = TPV; o < 32; o <<= 1) {
 #pragma unroll
@@ -297,7 +324,12 @@ __device__ __forceinline__ void vertex_update(const SweepParams& p, const Smem& 
         hit = um != 0ull;
     } else if (valid) {
         hit = __ldcg(p.upflag + v) != 0;
-        gather<K, LPT, TPV, 1>(acc, p.d, arcs, a, e, sub);
+        uint32_t b = a;
+        if (pre.on) {
+            if (b < e) gather_round<K, LPT, TPV>(acc, p.d, pre.q, b + 1 < e, b + 2 < e, b + 3 < e, sub);
+            b += 4;
+        }
+        gather<K, LPT, TPV, 1>(acc, p.d, arcs, b, e, sub);
         if (hit) um = __ldcg(p.upmask + v);
     }
     if (hit) {
@@ -339,25 +371,43 @@ __device__ void sweep_levels_cta(const SweepParams& p, const Smem& sm, int lo_le
 }
 
 // Level j, swept by all CTAs together: a warp per vertex if the level has no
-// more vertices than the grid has warps, else a group of TPV threads per vertex.
-template <int K, int TPV>
-__device__ void sweep_level_grid(const SweepParams& p, const Smem& sm, int j, int warp, int tid) {
+// more vertices than the grid has warps, else a group of TPV threads per
+// vertex (the level then fits one pass: narrow levels have fewer vertices
+// than the grid has groups).  plan_level reads what does not depend on the
+// labels -- the vertex's arc range and first round of arcs -- so that it can
+// run before the barrier that ends the previous level; finish_level gathers.
+struct LevelPlan {
+    int v;
+    bool valid, wpv;
+    uint32_t a, e;
+    FirstRound pre;
+};
+
+template <int TPV>
+__device__ __forceinline__ LevelPlan plan_level(const SweepParams& p, int j, int warp, int tid) {
+    constexpr int GPV = 32 / TPV;
+    LevelPlan pl;
     const int lo = __ldg(p.level_off + j), hi = __ldg(p.level_off + j + 1);
-    const bool store = p.write_all || j != p.last_level_block;
     const int warps = (int)gridDim.x * (kThreads / 32);
-    if (hi - lo <= warps) {
-        const int v = lo + (int)blockIdx.x * (kThreads / 32) + warp;
-        if (v < hi)  // warp-uniform
-            vertex_update<K, TPV, true>(p, sm, v, true, __ldg(p.down_off + v), __ldg(p.down_off + v + 1), p.down_arc,
-                                        store, tid);
+    pl.wpv = hi - lo <= warps;
+    pl.v = pl.wpv ? lo + (int)blockIdx.x * (kThreads / 32) + warp : lo + (int)blockIdx.x * (kThreads / TPV) + tid / TPV;
+    pl.valid = pl.v < hi;
+    pl.a = pl.valid ? __ldg(p.down_off + pl.v) : 0u;
+    pl.e = pl.valid ? __ldg(p.down_off + pl.v + 1) : 0u;
+    pl.pre.on = true;
+    if (pl.wpv) arcs_of_round<GPV>(pl.pre.q, p.down_arc, pl.a + (uint32_t)((tid & 31) / TPV), pl.e);
+    else arcs_of_round<1>(pl.pre.q, p.down_arc, pl.a, pl.e);
+    return pl;
+}
+
+template <int K, int TPV>
+__device__ __forceinline__ void finish_level(const SweepParams& p, const Smem& sm, int j, const LevelPlan& pl, int tid) {
+    const bool store = p.write_all || j != p.last_level_block;
+    if (pl.wpv) {
+        if (pl.valid)  // warp-uniform
+            vertex_update<K, TPV, true>(p, sm, pl.v, true, pl.a, pl.e, p.down_arc, store, tid, pl.pre);
     } else {
-        const int groups = (int)gridDim.x * (kThreads / TPV);
-        for (int b = lo; b < hi; b += groups) {  // uniform bounds: every thread takes part in the shuffles
-            const int v = b + (int)blockIdx.x * (kThreads / TPV) + tid / TPV;
-            const bool valid = v < hi;
-            vertex_update<K, TPV, false>(p, sm, v, valid, valid ? __ldg(p.down_off + v) : 0u,
-                                         valid ? __ldg(p.down_off + v + 1) : 0u, p.down_arc, store, tid);
-        }
+        vertex_update<K, TPV, false>(p, sm, pl.v, pl.valid, pl.a, pl.e, p.down_arc, store, tid, pl.pre);
     }
 }
 
@@ -409,17 +459,23 @@ __device__ __forceinline__ void process_chunk(const SweepParams& p, const Smem& 
     const Meta mt = sm.meta[stage];
     const int mode = (mt.flags >> 1) & 1;
     const int ob = mt.v0 & ~3;
-    const int v = mode ? mt.v0 + warp : mt.v0 + tid / TPV;
-    const bool valid = v < mt.v1;
     const bool store = p.write_all || mt.level != p.last_level_block;
-    uint32_t a = 0, e = 0;
-    if (valid) {
-        a = sm.offs[stage][v - ob];
-        e = sm.offs[stage][v + 1 - ob];
-    }
     const int2* arcs = (mt.flags & 1) ? p.down_arc : sm.arcs[stage] - mt.abase;
-    if (mode) vertex_update<K, TPV, true>(p, sm, v, valid, a, e, arcs, store, tid);
-    else vertex_update<K, TPV, false>(p, sm, v, valid, a, e, arcs, store, tid);
+    if (mode) {
+        const int v = mt.v0 + warp;
+        const bool valid = v < mt.v1;
+        const uint32_t a = valid ? sm.offs[stage][v - ob] : 0u, e = valid ? sm.offs[stage][v + 1 - ob] : 0u;
+        vertex_update<K, TPV, true>(p, sm, v, valid, a, e, arcs, store, tid);
+        return;
+    }
+    // kRounds vertices per thread group, one after the other
+#pragma unroll 1
+    for (int r = 0; r < kRounds; ++r) {
+        const int v = mt.v0 + r * (kConsumers / TPV) + tid / TPV;
+        const bool valid = v < mt.v1;
+        const uint32_t a = valid ? sm.offs[stage][v - ob] : 0u, e = valid ? sm.offs[stage][v + 1 - ob] : 0u;
+        vertex_update<K, TPV, false>(p, sm, v, valid, a, e, arcs, store, tid);
+    }
 }
 
 // Bookkeeping of a polling loop that found nothing to do (lane 0 decides):
@@ -460,8 +516,8 @@ __device__ __forceinline__ void release_chunk(const SweepParams& p, Smem& sm, in
 }
 
 template <int K, int TPV>
-__global__ void __launch_bounds__(kThreads, 1) k_sweep_tma(SweepParams p) {
-    constexpr int VPB = kConsumers / TPV;
+__global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_sweep_tma(SweepParams p) {
+    constexpr int VPB = kRounds * kConsumers / TPV;
     static_assert(VPB + 5 <= kOffCap, "offset buffer");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
@@ -494,14 +550,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_sweep_tma(SweepParams p) {
     // chunks of these levels and no dependencies on them.
     if (p.sync_levels > 0) {
         bool ok = true;
+        // plans read graph data only, so each is made before the barrier that
+        // ends the level in front of it
+        const bool grid_levels = p.solo_levels < p.sync_levels;
+        LevelPlan pl{};
+        if (grid_levels) pl = plan_level<TPV>(p, p.solo_levels, warp, tid);
         if (p.solo_levels > 0) {
             if (blockIdx.x == 0) sweep_levels_cta<K, TPV>(p, sm, 0, p.solo_levels, warp, tid);
             ok = grid_sync(p);
         }
         for (int j = p.solo_levels; ok && j < p.sync_levels; ++j) {
-            sweep_level_grid<K, TPV>(p, sm, j, warp, tid);
+            finish_level<K, TPV>(p, sm, j, pl, tid);
+            if (j + 1 < p.sync_levels) pl = plan_level<TPV>(p, j + 1, warp, tid);
             ok = grid_sync(p);
-            if (ok && p.trace && tid == 0 && blockIdx.x == 0) atomicMax((unsigned long long*)p.trace + 1 + j, global_ns());
+            if (ok && p.trace && tid == 0 && blockIdx.x == 0)
+                atomicMax((unsigned long long*)p.trace + 1 + j, global_ns());
         }
         if (!ok) return;  // the same in every thread of the CTA
     }
@@ -711,7 +774,7 @@ cudaError_t iso_launch_sweep_tma(const isod::SweepParams& p, int K, int tpv, int
 
 int iso_sweep_tma_occupancy(int K, int tpv, int* block, int* vpb) {
     *block = kThreads;
-    *vpb = kConsumers / tpv;
+    *vpb = kRounds * kConsumers / tpv;
 #define X(k, t) if (K == k && tpv == t) return occupancy<k, t>();
     ISO_TMA_CASES(X)
 #undef X
