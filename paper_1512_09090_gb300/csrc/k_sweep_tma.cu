@@ -45,10 +45,15 @@ using namespace isod;
 constexpr int kThreads = 1024;           // per CTA; 1024 / kThreads CTAs per SM
 constexpr int kConsumers = kThreads - 32;  // all warps but the last consume; the last produces
 constexpr int kStages = 3;               // chunks a CTA holds at once; warps take any ready one
-constexpr int kArcCap = 1536;            // arcs per stage buffer (larger chunks read arcs from HBM)
+constexpr int kArcCap = 3072;            // arcs per stage buffer (larger chunks read arcs from HBM)
 constexpr int kOffCap = 1024;            // offsets per stage buffer (>= VPB + 5)
 constexpr int kPredCap = 128;            // dependency list held per stage (longer lists stay in HBM)
-constexpr int kRounds = 1;               // vertices per thread group in a chunk of a wide level
+constexpr int kRounds = 2;               // vertices per thread group in a chunk of a wide level
+
+// Rounds per chunk for a group size: kRounds where the chunk's offsets fit the
+// stage buffer, else one.
+template <int TPV>
+__host__ __device__ constexpr int rounds_of() { return kRounds * (kConsumers / TPV) + 5 <= kOffCap ? kRounds : 1; }
 
 template <int K> struct MaskOf { using T = uint8_t; };
 template <> struct MaskOf<16> { using T = uint16_t; };
@@ -372,12 +377,12 @@ __device__ void sweep_levels_cta(const SweepParams& p, const Smem& sm, int lo_le
 
 // Level j, swept by all CTAs together: a warp per vertex if the level has no
 // more vertices than the grid has warps, else a group of TPV threads per
-// vertex (the level then fits one pass: narrow levels have fewer vertices
-// than the grid has groups).  plan_level reads what does not depend on the
-// labels -- the vertex's arc range and first round of arcs -- so that it can
-// run before the barrier that ends the previous level; finish_level gathers.
+// vertex, in as many passes over the grid's groups as the level needs.
+// plan_level reads what does not depend on the labels -- the arc range and
+// first round of arcs of the thread's first vertex -- so that it can run
+// before the barrier that ends the previous level; finish_level gathers.
 struct LevelPlan {
-    int v;
+    int v, hi;
     bool valid, wpv;
     uint32_t a, e;
     FirstRound pre;
@@ -390,6 +395,7 @@ __device__ __forceinline__ LevelPlan plan_level(const SweepParams& p, int j, int
     const int lo = __ldg(p.level_off + j), hi = __ldg(p.level_off + j + 1);
     const int warps = (int)gridDim.x * (kThreads / 32);
     pl.wpv = hi - lo <= warps;
+    pl.hi = hi;
     pl.v = pl.wpv ? lo + (int)blockIdx.x * (kThreads / 32) + warp : lo + (int)blockIdx.x * (kThreads / TPV) + tid / TPV;
     pl.valid = pl.v < hi;
     pl.a = pl.valid ? __ldg(p.down_off + pl.v) : 0u;
@@ -408,6 +414,13 @@ __device__ __forceinline__ void finish_level(const SweepParams& p, const Smem& s
             vertex_update<K, TPV, true>(p, sm, pl.v, true, pl.a, pl.e, p.down_arc, store, tid, pl.pre);
     } else {
         vertex_update<K, TPV, false>(p, sm, pl.v, pl.valid, pl.a, pl.e, p.down_arc, store, tid, pl.pre);
+        // further passes (uniform bounds: every thread takes part in the shuffles)
+        const int groups = (int)gridDim.x * (kThreads / TPV);
+        for (int v = pl.v + groups; v - (tid / TPV) < pl.hi; v += groups) {
+            const bool valid = v < pl.hi;
+            vertex_update<K, TPV, false>(p, sm, v, valid, valid ? __ldg(p.down_off + v) : 0u,
+                                         valid ? __ldg(p.down_off + v + 1) : 0u, p.down_arc, store, tid);
+        }
     }
 }
 
@@ -470,7 +483,7 @@ __device__ __forceinline__ void process_chunk(const SweepParams& p, const Smem& 
     }
     // kRounds vertices per thread group, one after the other
 #pragma unroll 1
-    for (int r = 0; r < kRounds; ++r) {
+    for (int r = 0; r < rounds_of<TPV>(); ++r) {
         const int v = mt.v0 + r * (kConsumers / TPV) + tid / TPV;
         const bool valid = v < mt.v1;
         const uint32_t a = valid ? sm.offs[stage][v - ob] : 0u, e = valid ? sm.offs[stage][v + 1 - ob] : 0u;
@@ -517,7 +530,7 @@ __device__ __forceinline__ void release_chunk(const SweepParams& p, Smem& sm, in
 
 template <int K, int TPV>
 __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_sweep_tma(SweepParams p) {
-    constexpr int VPB = kRounds * kConsumers / TPV;
+    constexpr int VPB = rounds_of<TPV>() * (kConsumers / TPV);
     static_assert(VPB + 5 <= kOffCap, "offset buffer");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
@@ -774,8 +787,7 @@ cudaError_t iso_launch_sweep_tma(const isod::SweepParams& p, int K, int tpv, int
 
 int iso_sweep_tma_occupancy(int K, int tpv, int* block, int* vpb) {
     *block = kThreads;
-    *vpb = kRounds * kConsumers / tpv;
-#define X(k, t) if (K == k && tpv == t) return occupancy<k, t>();
+#define X(k, t) if (K == k && tpv == t) { *vpb = rounds_of<t>() * (kConsumers / t); return occupancy<k, t>(); }
     ISO_TMA_CASES(X)
 #undef X
     return 0;

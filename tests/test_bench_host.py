@@ -1,0 +1,41 @@
+"""Host-side checks of bench.py: the reference arm (the oracle on host cores)
+prints one JSON line with the fields the measurement contract asks for, and
+the algorithmic byte count of a sweep follows its definition."""
+
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_json_line():
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "grid1k_k16",
+                        "--steps", "2", "--warmup", "1"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [x for x in r.stdout.splitlines() if x.startswith("{")]
+    assert len(lines) == 1
+    j = json.loads(lines[0])
+    assert j["impl"] == "reference" and j["unit"] == "queries/s" and j["higher_is_better"] is True
+    assert j["value"] > 0 and j["steps"] >= 1 and j["config"]["workload"] == "grid1k_k16"
+    cb = j["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == j["value"] and cb["sample"]
+    assert j["e2e"] == {"value": j["value"], "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_sweep_bytes_definition():
+    sys.path.insert(0, ROOT)
+    import bench
+    # a 6-vertex toy: three levels; downward arcs from sources 0, 0, 1, 2
+    A = {"perm": np.arange(6), "level_off": np.array([0, 1, 3, 6]), "down_src": np.array([0, 0, 1, 2])}
+    b = bench.sweep_bytes(A, 64)
+    n, k = 6, 64
+    assert b["offsets"] == 4 * (n + 1)
+    assert b["arcs"] == 8 * 4
+    assert b["d_write"] == 4 * k * (n - 3)       # the lowest level (3 vertices) stores no rows
+    assert b["d_read"] == 4 * k * 3              # distinct sources 0, 1, 2
+    assert b["mask_write"] == 8 * n and b["upflag_read"] == n
+    assert bench.sweep_bytes(A, 64, write_all=True)["d_write"] == 4 * k * n

@@ -135,10 +135,12 @@ def test_top_block_sizes(solo, graph):
     check_batch(g, dg, srcs, taus, solo_width=solo, use_cuda_graph=graph, sweep_kernel=1)
 
 
-@pytest.mark.parametrize("solo,fuse", [(-1, -1), (124, -1), (-1, 0), (1 << 30, 0)])
+@pytest.mark.parametrize("solo,fuse", [(-1, -1), (124, -1), (-1, 0), (1 << 30, 0), (124, 1 << 20), (-1, 1 << 20)])
 def test_leading_level_phases(solo, fuse):
     # fuse -1: no level-synchronous phase (every level in the chunk schedule);
-    # solo -1 with the default fuse width: all narrow levels under grid barriers
+    # solo -1 with the default fuse width: all narrow levels under grid barriers;
+    # fuse 1 << 20: every level grid-synchronous, the widest ones in several
+    # passes over the grid's thread groups
     g, dg = dev_graph("grid1k")
     srcs = synth.draw_sources(g, 16, 61)
     taus = synth.draw_taus_uniform(16, 0, 60000, 62)
