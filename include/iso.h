@@ -139,9 +139,12 @@ void iso_free_graph(iso_graph* g);
 typedef struct {
     int32_t threads_per_vertex; /* sweep threads per vertex (each owns K/threads lanes); 0 = auto */
     int32_t ctas_per_sm;        /* persistent sweep CTAs per SM; 0 = auto (occupancy) */
-    int32_t fuse_width;         /* narrow-level threshold: the plain sweep runs levels with fewer
-                                   vertices in one CTA between grid barriers; the TMA-staged sweep
-                                   gives them a warp per vertex.  0 = auto, -1 = never */
+    int32_t fuse_width;         /* narrow-level threshold.  Plain sweep: levels with fewer vertices
+                                   run in one CTA between grid barriers.  TMA-staged sweep: the
+                                   leading levels with fewer vertices are swept level by level with
+                                   a grid barrier each before the chunk schedule starts (0 = auto:
+                                   one chunk per CTA), later ones get a warp per vertex.
+                                   -1 = never */
     int32_t use_cuda_graph;     /* 1 = capture the launch sequence once per workspace and replay */
     int64_t barrier_timeout_ns; /* give up a grid barrier after this long; 0 = 2 s */
     int32_t debug_barrier_extra;/* testing only: the sweep's barriers wait for this many extra

@@ -46,11 +46,13 @@ class IsoServer:
 
     lanes: queries per batch (1..64).  workspaces: number of batches in flight;
     None = as many as fit in `memory_fraction` of the free device memory (at
-    most max_workspaces).  Extra keyword options go to the workspaces
-    (iso_query_opts fields)."""
+    most max_workspaces).  warm: run one small batch on every workspace before
+    taking requests, so that no request waits for a workspace's first launch
+    (CUDA-graph capture, sweep schedule upload).  Extra keyword options go to
+    the workspaces (iso_query_opts fields)."""
 
     def __init__(self, g: _lib.DeviceGraph, lanes: int = 64, workspaces: int | None = None,
-                 memory_fraction: float = 0.5, max_workspaces: int = 4, **opts):
+                 memory_fraction: float = 0.5, max_workspaces: int = 4, warm: bool = True, **opts):
         import torch
         self.g = g
         self.lanes = lanes
@@ -69,6 +71,12 @@ class IsoServer:
             workspaces = max(1, min(max_workspaces, 1 + fit))
         self.workspaces = [first] + [_lib.Workspace(g, lanes, **opts) for _ in range(workspaces - 1)]
         self.bytes_per_workspace = per_ws
+        if warm:
+            src = np.zeros(lanes, np.int32)
+            tau = np.zeros(lanes, np.int32)
+            for ws in self.workspaces:
+                ws.submit(src, tau)
+                ws.collect()
         self._threads = [threading.Thread(target=self._worker, args=(ws,), daemon=True) for ws in self.workspaces]
         for t in self._threads:
             t.start()
