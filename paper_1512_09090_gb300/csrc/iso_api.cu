@@ -68,8 +68,8 @@ bool is_device_ptr(const void* p) {
 }
 
 constexpr int kMaxLanes = 64;
-// default size limit of the levels in the top block of the TMA sweep (four
-// vertices per consumer warp)
+// default size limit of the top levels that CTA 0 sweeps alone in the TMA
+// sweep (four vertices per consumer warp)
 constexpr int kSoloWidth = 124;
 
 int lanes_class(int k) {
