@@ -42,6 +42,27 @@ WORKLOADS = {
     "grid1k_k16": dict(graph="grid1k", k=16, tau=("choice", (2000, 10000, 50000))),
     "grid1k_k64": dict(graph="grid1k", k=64, tau=("uniform", 2000, 50000)),
 }
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one sweep launch
+# from one ncu capture per workload, with the hash of the sweep's sources that
+# capture ran; reported as the roofline's traffic only while the hash matches.
+SWEEP_TRAFFIC = {"grid18m_k64": ("cfa0a6bff1b50d62", 15_270_385_152 + 3_365_787_136)}
+SWEEP_SOURCES = ("k_sweep_tma.cu", "iso_device.cuh", "schedule.cpp")
+
+
+def sweep_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in SWEEP_SOURCES:
+        with open(os.path.join(ROOT, "paper_1512_09090_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def sweep_traffic(workload):
+    rec = SWEEP_TRAFFIC.get(workload)
+    return rec[1] if rec and rec[0] == sweep_source_hash() else None
+
+
 METRIC = "isochrone queries/s on 18M-vertex graph (1 GB300); sweep HBM GB/s vs peak; p99 ms"
 CACHE = os.path.join(ROOT, "paper_1512_09090_gb300", "_cache")
 
@@ -421,7 +442,7 @@ def main():
     peak, src = peaks()
     achieved = alg / (sw / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": None, "kernel": "k_sweep",
+            "frac": round(achieved / peak, 4), "traffic": sweep_traffic(args.workload), "kernel": "k_sweep",
             "alg_bytes_per_launch": alg, "peak_source": src, "sweep_ms": round(sw, 4)}
     lat = sorted(pipelined["latency_ms"])
     line = {"metric": METRIC, "value": round(value, 2), "unit": "queries/s", "n_gpus": world, "steps": args.steps,

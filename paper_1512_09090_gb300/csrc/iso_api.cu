@@ -20,6 +20,7 @@
 #include "iso_device.cuh"
 #include "sweep_schedule.h"
 #include "../../include/iso.h"
+#include "graph_view.h"
 
 namespace {
 
@@ -824,16 +825,6 @@ extern "C" int iso_query(iso_graph* g, int32_t k, const int32_t* sources, const 
         iso::set_error("iso_query: %lld arcs do not fit capacity %lld", (long long)used, (long long)cap);
     return result;
 }
-
-// Read-only view of a device graph for the allocation-free entry point.
-struct iso_graph_view {
-    int n, L, tau_max, num_sms;
-    int64_t m;
-    const uint32_t *down_off, *up_off, *orig_off;
-    const int2 *down_arc, *up_arc;
-    const int32_t *orig_head, *orig_id, *pos, *level_off, *emit_tail;
-    const int32_t* h_level_off;
-};
 
 int iso_graph_view_of(const iso_graph* g, iso_graph_view* v) {
     if (!g || !v) return ISO_E_INVAL;

@@ -29,6 +29,7 @@
 #include <mutex>
 
 #include "ch_internal.h"
+#include "graph_view.h"
 #include "iso_device.cuh"
 #include "../../include/iso.h"
 
@@ -84,17 +85,6 @@ int fail(int code, const char* what, cudaError_t e) {
 }  // namespace
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
-
-// Fields of iso_graph needed here (the struct is defined in iso_api.cu).
-struct iso_graph_view {
-    int n, L, tau_max, num_sms;
-    int64_t m;
-    const uint32_t *down_off, *up_off, *orig_off;
-    const int2 *down_arc, *up_arc;
-    const int32_t *orig_head, *orig_id, *pos, *level_off, *emit_tail;
-    const int32_t* h_level_off;
-};
-int iso_graph_view_of(const iso_graph* g, iso_graph_view* v);
 
 extern "C" int iso_query_noalloc(iso_graph* g, int32_t k, const int32_t* sources, const int32_t* taus,
                                  int64_t* out_offsets, int32_t* out_arcs, int64_t cap, void* stream_) {

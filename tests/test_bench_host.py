@@ -39,3 +39,12 @@ def test_sweep_bytes_definition():
     assert b["d_read"] == 4 * k * 3              # distinct sources 0, 1, 2
     assert b["mask_write"] == 8 * n and b["upflag_read"] == n
     assert bench.sweep_bytes(A, 64, write_all=True)["d_write"] == 4 * k * n
+
+
+def test_traffic_only_for_the_captured_sources():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.sweep_traffic("no-such-workload") is None
+    h, t = bench.SWEEP_TRAFFIC["grid18m_k64"]
+    got = bench.sweep_traffic("grid18m_k64")
+    assert got == (t if h == bench.sweep_source_hash() else None)
