@@ -49,6 +49,21 @@ SWEEP_TRAFFIC = {"grid18m_k64": ("cfa0a6bff1b50d62", 15_270_385_152 + 3_365_787_
 SWEEP_SOURCES = ("k_sweep_tma.cu", "iso_device.cuh", "schedule.cpp")
 
 
+def max_over_ranks(x, dist=None, device="cpu"):
+    """Largest x over all ranks (the job's time is its slowest rank's); x itself without a process group."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, queries_per_step, steps, seconds):
+    """Whole-job queries/s: every rank answers its own queries (replicas, weak scaling)."""
+    return world * queries_per_step * steps / seconds
+
+
 def sweep_source_hash():
     import hashlib
     h = hashlib.sha256()
@@ -380,11 +395,9 @@ def main():
             log(f"[trace] {st[0]} {st[1]}-{st[2]} {nv} {(t - prev) / 1e3:.1f}")
             prev = max(prev, t)
     if dist:
-        tt = torch.tensor([el_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        el_ms = float(tt.item())
+        el_ms = max_over_ranks(el_ms, dist, "cuda")
         dist.barrier()
-    value = world * k * args.steps / (el_ms / 1e3)
+    value = job_throughput(world, k, args.steps, el_ms / 1e3)
 
     # end to end through the public call with host buffers (pinned)
     e2e = None
@@ -408,10 +421,9 @@ def main():
             d2h += int(ho[-1]) * 4 + (k + 1) * 8
         e2e_s = time.perf_counter() - t0
         if dist:
-            tt = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_s = float(tt.item())
-        e2e = {"value": world * k * args.steps / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": 2 * 4 * k,
+            e2e_s = max_over_ranks(e2e_s, dist, "cuda")
+        e2e = {"value": job_throughput(world, k, args.steps, e2e_s), "unit": "queries/s",
+               "h2d_bytes_per_step": 2 * 4 * k,
                "d2h_bytes_per_step": d2h // args.steps}
 
     serving_stats = None
