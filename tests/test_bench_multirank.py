@@ -22,7 +22,7 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _rank_main(rank, world, port, out):
+def _rank_main(rank, world, port, outdir):
     sys.path.insert(0, ROOT)
     import bench
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
@@ -31,18 +31,20 @@ def _rank_main(rank, world, port, out):
         el_ms = 10.0 + 5.0 * rank                      # rank 1 is the slow one
         slowest = bench.max_over_ranks(el_ms, tdist, "cpu")
         value = bench.job_throughput(world, 64, 200, slowest / 1e3)
-        out[rank] = (slowest, value)
+        with open(os.path.join(outdir, f"rank{rank}.txt"), "w") as f:
+            f.write(f"{slowest!r} {value!r}")
     finally:
         tdist.destroy_process_group()
 
 
-def test_two_rank_timing_and_throughput():
+def test_two_rank_timing_and_throughput(tmp_path):
     world = 2
     port = _free_port()
-    with mp.Manager() as m:
-        out = m.dict()
-        mp.spawn(_rank_main, args=(world, port, out), nprocs=world, join=True)
-        res = dict(out)
+    mp.spawn(_rank_main, args=(world, port, str(tmp_path)), nprocs=world, join=True)
+    res = {}
+    for r in range(world):
+        a, b = (tmp_path / f"rank{r}.txt").read_text().split()
+        res[r] = (float(a), float(b))
     assert res[0] == res[1]                            # both ranks agree
     slowest, value = res[0]
     assert slowest == 15.0
