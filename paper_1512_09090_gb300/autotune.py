@@ -71,7 +71,7 @@ def tune(g: _lib.DeviceGraph, sources: np.ndarray, taus: np.ndarray, lanes_choic
     cands = []
     for lanes in lanes_choices:
         for tpv in TPV_CHOICES.get(lanes, (1,)):
-            for rounds in (2, 4, 8):  # schedule delay in rounds of one chunk per CTA
+            for rounds in (1, 2, 4, 8):  # schedule delay in rounds of one chunk per CTA
                 cands.append({"lanes": lanes, "threads_per_vertex": tpv, "schedule_delay": rounds * sms})
     start = time.perf_counter()
     best, best_qps, tried = None, -1.0, []
