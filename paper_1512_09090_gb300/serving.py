@@ -56,10 +56,7 @@ class IsoServer:
         import torch
         self.g = g
         self.lanes = lanes
-        self._q: queue.Queue = queue.Queue()
-        self._stop = threading.Event()
-        self._batch_id = 0
-        self._id_lock = threading.Lock()
+        self._init_state()
         opts.setdefault("use_cuda_graph", 1)
         free0, _ = torch.cuda.mem_get_info()
         first = _lib.Workspace(g, lanes, **opts)
@@ -77,6 +74,29 @@ class IsoServer:
             for ws in self.workspaces:
                 ws.submit(src, tau)
                 ws.collect()
+        self._start_workers()
+
+    @classmethod
+    def over_workspaces(cls, workspaces, lanes: int) -> "IsoServer":
+        """A server over ready-made workspaces: objects with submit(sources, taus)
+        and collect() -> (offsets, arcs, dist), as _lib.Workspace has.  No device
+        set-up happens here."""
+        self = cls.__new__(cls)
+        self.g = None
+        self.lanes = lanes
+        self._init_state()
+        self.workspaces = list(workspaces)
+        self.bytes_per_workspace = 0
+        self._start_workers()
+        return self
+
+    def _init_state(self):
+        self._q: queue.Queue = queue.Queue()
+        self._stop = threading.Event()
+        self._batch_id = 0
+        self._id_lock = threading.Lock()
+
+    def _start_workers(self):
         self._threads = [threading.Thread(target=self._worker, args=(ws,), daemon=True) for ws in self.workspaces]
         for t in self._threads:
             t.start()
