@@ -38,7 +38,7 @@ extern "C" {
 #define ISO_E_NOMEM     2  /* host or device allocation failed */
 #define ISO_E_OVERFLOW  3  /* output capacity too small; offsets hold the sizes needed */
 #define ISO_E_CUDA      4  /* a CUDA runtime call or kernel launch failed */
-#define ISO_E_TIMEOUT   5  /* a device-side grid barrier gave up waiting; results are invalid */
+#define ISO_E_TIMEOUT   5  /* a device-side wait (grid barrier or dependency flag) gave up; results are invalid */
 #define ISO_E_IO        6  /* file could not be read or written, or is not a CH file */
 #define ISO_E_NODEV     7  /* no usable CUDA device (the library never falls back to the CPU) */
 
@@ -146,9 +146,11 @@ typedef struct {
                                    one chunk per CTA), later ones get a warp per vertex.
                                    -1 = never */
     int32_t use_cuda_graph;     /* 1 = capture the launch sequence once per workspace and replay */
-    int64_t barrier_timeout_ns; /* give up a grid barrier after this long; 0 = 2 s */
-    int32_t debug_barrier_extra;/* testing only: the sweep's barriers wait for this many extra
-                                   arrivals that never come, so every wait times out */
+    int64_t barrier_timeout_ns; /* give up a device-side wait (grid barrier, dependency flag, copy)
+                                   after this long without progress; 0 = 2 s */
+    int32_t debug_barrier_extra;/* testing only: the sweep's barriers and dependency checks wait
+                                   for this many extra arrivals or flags that never come, so the
+                                   sweep times out */
     int32_t sweep_kernel;       /* 0 = auto (TMA-staged arc blocks), 1 = TMA-staged, 2 = plain loads */
     int32_t record_trace;       /* 1 = record the device time of every sweep step (iso_workspace_trace) */
     int32_t schedule_delay;     /* TMA-staged sweep: a chunk is scheduled at least this many positions
@@ -198,11 +200,12 @@ int iso_workspace_timings(const iso_workspace* ws, float* ms4);
 /* Per-level times of the last collected batch (workspaces created with
  * record_trace = 1 and the TMA-staged sweep).  Entry i < L: steps4[4i..4i+3] =
  * {0, i, i+1, 0} and ns[i] = device nanoseconds from the start of the sweep
- * until the last chunk of level block i was complete (blocks in sweep order,
- * block 0 = top level; the sweep interleaves levels, so these need not grow).
- * Entry L: steps4 = {2, 0, 0, 0} and ns[L] = time spent loading the upward
- * labels before the walk.  Returns L+1 (at most cap entries are written) or -1
- * on error. */
+ * until level block i was complete (blocks in sweep order, block 0 = top
+ * level; below the leading levels the sweep interleaves levels, so these need
+ * not grow).  Entry L: steps4 = {2, 0, 0, 0} and ns[L] = time before the walk
+ * over the levels starts (0: the upward search writes its labels straight into
+ * the label rows).  Returns L+1 (at most cap entries are written) or -1 on
+ * error. */
 int32_t iso_workspace_trace(const iso_workspace* ws, int32_t* steps4, int64_t* ns, int32_t cap);
 void iso_free_workspace(iso_workspace* ws);
 

@@ -28,7 +28,7 @@ void clear_error() { g_last_error.clear(); }
 }  // namespace iso
 
 extern "C" const char* iso_last_error(void) { return iso::g_last_error.c_str(); }
-extern "C" const char* iso_version(void) { return "iso-gb300 0.1 (sm_103a)"; }
+extern "C" const char* iso_version(void) { return "iso-gb300 0.2 (sm_103a)"; }
 
 namespace {
 const char kMagic[8] = {'I', 'S', 'O', 'C', 'H', 0, 0, 2};
