@@ -125,6 +125,23 @@ extern "C" int iso_load_ch(const char* path, iso_ch** out) {
             for (int32_t x : ch->orig_id) if (x < 0 || x >= ch->m) { ok = false; break; }
             for (int32_t x : ch->down_w) if (x < 0) { ok = false; break; }
             for (int32_t x : ch->up_w) if (x < 0) { ok = false; break; }
+            // the BFS ranks are a permutation (emission lays tails out by them)
+            std::vector<char> seen(n, 0);
+            for (int32_t x : ch->bfs) {
+                if (seen[(size_t)x]) { ok = false; break; }
+                seen[(size_t)x] = 1;
+            }
+            // every downward arc comes from a higher level and every upward arc
+            // goes to one: the sweep's order depends on it (level block 0 = top)
+            std::vector<int32_t> block(n);
+            for (int32_t j = 0; j < ch->L && ok; ++j)
+                for (int32_t v = ch->level_off[j]; v < ch->level_off[j + 1]; ++v) block[(size_t)v] = j;
+            for (size_t v = 0; v < n && ok; ++v) {
+                for (int64_t a = ch->down_off[v]; a < ch->down_off[v + 1]; ++a)
+                    if (block[(size_t)ch->down_src[(size_t)a]] >= block[v]) { ok = false; break; }
+                for (int64_t a = ch->up_off[v]; a < ch->up_off[v + 1] && ok; ++a)
+                    if (block[(size_t)ch->up_dst[(size_t)a]] >= block[v]) { ok = false; break; }
+            }
         }
     }
     std::fclose(f);

@@ -117,6 +117,35 @@ def test_ch_save_load_roundtrip(tmp_path):
         P.iso_load_ch(path)
 
 
+def _corrupt_and_load(path, raw, offset, value):
+    b = bytearray(raw)
+    b[offset:offset + 4] = np.array([value], np.int32).tobytes()
+    open(path, "wb").write(bytes(b))
+    with pytest.raises(IsoError) as e:
+        P.iso_load_ch(path)
+    return e.value.code
+
+
+def test_load_rejects_well_formed_but_inconsistent_files(tmp_path):
+    # file layout: 8-byte magic, 4 int32 + 4 int64 header, perm[n], bfs[n],
+    # level_off[L+1] (int32), down_off[n+1] (int64), down_src[m_down], ...
+    g, ch = workload("grid64")
+    path = str(tmp_path / "g.ch")
+    ch.save(path)
+    raw = open(path, "rb").read()
+    A = ch.arrays()
+    n, L = g.n, len(A["level_off"]) - 1
+    bfs_at = 56 + 4 * n
+    # BFS ranks that are not a permutation
+    assert _corrupt_and_load(path, raw, bfs_at + 4, int(A["bfs"][0])) == P.ISO_E_IO
+    # a downward arc from a vertex of the lowest level
+    src_at = bfs_at + 4 * n + 4 * (L + 1) + 8 * (n + 1)
+    assert _corrupt_and_load(path, raw, src_at, n - 1) == P.ISO_E_IO
+    # the unmodified file still loads
+    open(path, "wb").write(raw)
+    assert P.iso_load_ch(path).stats()["n"] == n
+
+
 def test_build_rejects_bad_input():
     t = np.array([0, 1], np.int32); h = np.array([1, 2], np.int32); w = np.array([1, 1], np.int32)
     for args in [(0, t, h, w), (2, t, h, w), (3, t, h, np.array([1, -1], np.int32)),
