@@ -313,6 +313,11 @@ extern "C" int iso_build_ch(int32_t n, int64_t m, const int32_t* tail, const int
     const int settle_limit = (opts && opts->witness_settle_limit > 0) ? opts->witness_settle_limit : 400;
     const int prio_limit = (opts && opts->priority_settle_limit > 0) ? opts->priority_settle_limit : 0;
     auto t0 = std::chrono::steady_clock::now();
+    // ISO_CH_VERBOSE in the environment: phase and per-round timings on stderr
+    const bool verbose = std::getenv("ISO_CH_VERBOSE") != nullptr;
+    auto since = [](std::chrono::steady_clock::time_point a) {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - a).count();
+    };
 
     std::unique_ptr<iso_ch> ch;
     try {
@@ -342,6 +347,7 @@ extern "C" int iso_build_ch(int32_t n, int64_t m, const int32_t* tail, const int
             }
         }
 
+        if (verbose) std::fprintf(stderr, "BFS numbering %.2f s\n", since(t0));
         Graph g;
         g.n = n;
         g.adj.resize(n);
@@ -362,6 +368,8 @@ extern "C" int iso_build_ch(int32_t n, int64_t m, const int32_t* tail, const int
             }
         }
 
+        if (verbose) std::fprintf(stderr, "setup (BFS numbering, adjacency) %.2f s\n", since(t0));
+        auto tp = std::chrono::steady_clock::now();
         std::vector<int32_t> level(n, 0), cn(n, 0);
         std::vector<int64_t> prio(n, 0);
         std::vector<uint8_t> in_set(n, 0), dirty(n, 0), contracted(n, 0);
@@ -381,7 +389,8 @@ extern "C" int iso_build_ch(int32_t n, int64_t m, const int32_t* tail, const int
         std::vector<std::vector<int32_t>> dirty_buf(threads);
         int64_t shortcuts = 0;
 
-        const bool verbose = std::getenv("ISO_CH_VERBOSE") != nullptr;
+        if (verbose) std::fprintf(stderr, "initial priorities %.2f s\n", since(tp));
+        tp = std::chrono::steady_clock::now();
         int round = 0;
         while (!remaining.empty()) {
             auto tr0 = std::chrono::steady_clock::now();
@@ -469,6 +478,8 @@ extern "C" int iso_build_ch(int32_t n, int64_t m, const int32_t* tail, const int
             ++round;
         }
         ch->shortcuts = shortcuts;
+        if (verbose) std::fprintf(stderr, "contraction rounds %.2f s\n", since(tp));
+        tp = std::chrono::steady_clock::now();
 
         // ---- sweep order: descending level, BFS numbering within a level ----
         int32_t L = 0;
@@ -540,6 +551,7 @@ extern "C" int iso_build_ch(int32_t n, int64_t m, const int32_t* tail, const int
                 ch->orig_id[o] = (int32_t)e;
             }
         }
+        if (verbose) std::fprintf(stderr, "sweep order and CSRs %.2f s\n", since(tp));
     } catch (const std::bad_alloc&) {
         iso::set_error("iso_build_ch: out of host memory");
         return ISO_E_NOMEM;
