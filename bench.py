@@ -59,6 +59,20 @@ def max_over_ranks(x, dist=None, device="cpu"):
     return float(t.item())
 
 
+def first_on_rank0(fn, dist=None, rank=0):
+    """Run fn() on rank 0 first and on the other ranks after it: an expensive
+    step whose result rank 0 leaves in a shared cache (the contraction
+    hierarchy) is then done once per node instead of once per rank."""
+    if dist is None:
+        return fn()
+    if rank == 0:
+        out = fn()
+        dist.barrier()
+        return out
+    dist.barrier()
+    return fn()
+
+
 def job_throughput(world, queries_per_step, steps, seconds):
     """Whole-job queries/s: every rank answers its own queries (replicas, weak scaling)."""
     return world * queries_per_step * steps / seconds
@@ -291,8 +305,8 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    _build.build()
-    g, ch = load_graph_and_ch(spec["graph"])
+    first_on_rank0(_build.build, dist, local)   # in-tree library: one writer
+    g, ch = first_on_rank0(lambda: load_graph_and_ch(spec["graph"]), dist, local)
     A = ch.arrays()
     dg = P.iso_upload_graph(ch)
     k = spec["k"]

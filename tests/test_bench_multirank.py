@@ -51,8 +51,34 @@ def test_two_rank_timing_and_throughput(tmp_path):
     assert value == pytest.approx(2 * 64 * 200 / 0.015)
 
 
+def _order_main(rank, world, port, outdir):
+    sys.path.insert(0, ROOT)
+    import time
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    tdist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        def build():
+            if rank == 0:
+                time.sleep(0.5)                    # a slow build on rank 0
+            with open(os.path.join(outdir, "order.txt"), "a") as f:
+                f.write(f"{rank}\n")
+            return rank
+        assert bench.first_on_rank0(build, tdist, rank) == rank
+    finally:
+        tdist.destroy_process_group()
+
+
+def test_rank0_builds_before_the_others(tmp_path):
+    world = 3
+    mp.spawn(_order_main, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
+    order = (tmp_path / "order.txt").read_text().split()
+    assert order[0] == "0" and sorted(order) == ["0", "1", "2"]
+
+
 def test_single_rank_needs_no_group():
     sys.path.insert(0, ROOT)
     import bench
     assert bench.max_over_ranks(3.5) == 3.5
     assert bench.job_throughput(1, 64, 10, 0.5) == 1280.0
+    assert bench.first_on_rank0(lambda: 7) == 7
