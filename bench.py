@@ -45,7 +45,7 @@ WORKLOADS = {
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one sweep launch
 # from one ncu capture per workload, with the hash of the sweep's sources that
 # capture ran; reported as the roofline's traffic only while the hash matches.
-SWEEP_TRAFFIC = {"grid18m_k64": ("cfa0a6bff1b50d62", 15_270_385_152 + 3_365_787_136)}
+SWEEP_TRAFFIC = {"grid18m_k64": ("18cdeeeb333a59e0", 15_270_385_152 + 3_365_787_136)}
 SWEEP_SOURCES = ("k_sweep_tma.cu", "iso_device.cuh", "schedule.cpp")
 
 

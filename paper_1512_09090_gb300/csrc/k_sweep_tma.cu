@@ -8,34 +8,40 @@
 // lengths <= 0x7FFFFFFE.
 //
 // The upward search has already written each lane's labels into the rows
-// (upmask[v] says which lanes), so the walk starts at once.
+// (upmask[v] says which lanes), so the walk starts at once.  One persistent
+// kernel, launched cooperatively (every CTA resident), in two phases.
 //
-// Work is cut into chunks of VPB consecutive vertices of one level and run in
-// the order of a host-built schedule (schedule.cpp) that interleaves levels
-// region by region for L2 reuse; schedule position q belongs to CTA q mod G.
-// (Handing positions out dynamically from a global counter was measured
-// slower: a CTA then holds positions it cannot start for a whole window.)
-// Each CTA (1024 threads, one per SM) has 31 consumer warps and one producer
-// warp, and holds up to kStages chunks at once.
-// The producer copies each chunk's CSR offsets and its contiguous block of
-// incoming downward arcs into a free stage buffer with cp.async.bulk
-// (completing on the stage's "full" mbarrier) and caches the chunk's list of
-// dependencies (the schedule positions holding sources of its arcs) in shared
-// memory.  It never blocks: each pass it fills every free buffer, then reads
+// Leading levels.  The top of the hierarchy is a long chain of small levels.
+// CTA 0 alone sweeps those of at most solo_width vertices (a warp per vertex,
+// a CTA barrier per level); then all CTAs sweep the following narrow ones with
+// a bounded grid barrier per level, each thread reading its next vertex's arc
+// range and first arcs before the barrier that ends the level in front.
+//
+// Chunk schedule.  Every later level is cut into chunks of VPB consecutive
+// vertices (kRounds per thread group) and run in the order of a host-built
+// schedule (schedule.cpp) that interleaves levels region by region for L2
+// reuse; schedule position q belongs to CTA q mod G.  (Handing positions out
+// dynamically from a global counter was measured slower: a CTA then holds
+// positions it cannot start for a whole window.)  Each CTA (1024 threads, one
+// per SM) has 31 consumer warps and one producer warp and holds up to kStages
+// chunks at once.  Lane s of the producer owns stage s: once the buffer is
+// free it copies the chunk's CSR offsets, its contiguous block of incoming
+// downward arcs and its dependency list (the schedule positions holding
+// sources of its arcs) in with cp.async.bulk, completing on the stage's "full"
+// mbarrier.  It never blocks: each pass it fills every free buffer, then reads
 // the completion flags of all staged chunks in one batch of relaxed loads and
 // posts every chunk whose dependencies are all complete as ready.  Each
 // consumer warp works on any ready chunk among the oldest kStages it has not
 // done (oldest first), gathering rows d[u] with ld.global.cg, so one chunk
 // waiting for another CTA does not hold up the chunks behind it.  A warp
 // releases the buffer on the "empty" mbarrier; the last of the 31 to finish a
-// chunk marks its position complete.  There are no grid barriers.
-// Narrow levels use a warp per vertex: its groups of TPV threads take every
-// (32/TPV)-th arc, so a vertex with many arcs needs one round of gathers, and
-// chunks are 31 vertices so more CTAs share the level.
+// chunk marks its position complete.  A narrow level further down uses a warp
+// per vertex: its groups of TPV threads take every (32/TPV)-th arc, and chunks
+// are 31 vertices so more CTAs share the level.
 //
-// Every wait (mbarrier, dependency flags) is bounded: past the limit
-// the kernel records kStTimeout, stops issuing copies, waits (bounded) for the
-// copies it already issued, and returns.
+// Every wait (mbarrier, dependency flag, grid barrier) is bounded: past the
+// limit the kernel records kStTimeout, stops issuing copies, waits (bounded)
+// for the copies it already issued, and returns.
 #include "iso_device.cuh"
 
 namespace {
