@@ -45,7 +45,7 @@ WORKLOADS = {
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one sweep launch
 # from one ncu capture per workload, with the hash of the sweep's sources that
 # capture ran; reported as the roofline's traffic only while the hash matches.
-SWEEP_TRAFFIC = {"grid18m_k64": ("18cdeeeb333a59e0", 15_270_385_152 + 3_365_787_136)}
+SWEEP_TRAFFIC = {"grid18m_k64": ("6a8b1f134232b9de", 15_270_385_152 + 3_365_787_136)}
 SWEEP_SOURCES = ("k_sweep_tma.cu", "iso_device.cuh", "schedule.cpp")
 
 
@@ -279,7 +279,8 @@ def main():
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--sweep-kernel", type=int, default=0)
     ap.add_argument("--delay", type=int, default=0, help="schedule delay (TMA sweep)")
-    ap.add_argument("--solo", type=int, default=0, help="top-block level size limit (TMA sweep; -1 = none)")
+    ap.add_argument("--solo", type=int, default=0, help="top levels swept by CTA 0 alone: size limit (-1 = none)")
+    ap.add_argument("--span", type=int, default=0, help="largest BFS-rank span of a sweep chunk (0 = no limit)")
     ap.add_argument("--pipeline", type=int, default=3, help="batches in flight (workspaces, one stream each)")
     ap.add_argument("--trace", action="store_true", help="print per-step sweep times to stderr")
     ap.add_argument("--no-autotune", action="store_true")
@@ -323,7 +324,7 @@ def main():
                 opts[key] = tuned[key]
     for flag, key in ((args.tpv, "threads_per_vertex"), (args.delay, "schedule_delay"),
                       (args.sweep_kernel, "sweep_kernel"), (args.fuse, "fuse_width"),
-                      (args.ctas_per_sm, "ctas_per_sm"), (args.solo, "solo_width")):
+                      (args.ctas_per_sm, "ctas_per_sm"), (args.solo, "solo_width"), (args.span, "chunk_span")):
         if flag:
             opts[key] = flag
     if args.trace:

@@ -159,7 +159,10 @@ typedef struct {
                                    has at most this many vertices, run in one CTA level by level
                                    (CTA barriers instead of flags between CTAs); 0 = auto (124),
                                    -1 = never */
-    int32_t reserved[3];        /* must be zero */
+    int32_t chunk_span;         /* TMA-staged sweep: a chunk also ends where the BFS rank of its next
+                                   vertex is this far or more above its first one's, so that chunks
+                                   of sparse levels cover small parts of the map; 0 = no limit */
+    int32_t reserved[2];        /* must be zero */
 } iso_query_opts;
 
 /* Answer k isochrone queries (source sources[i], limit taus[i]) in sweeps of

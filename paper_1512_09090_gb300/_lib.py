@@ -65,7 +65,8 @@ class QueryOpts(ctypes.Structure):
                 ("fuse_width", ctypes.c_int32), ("use_cuda_graph", ctypes.c_int32),
                 ("barrier_timeout_ns", ctypes.c_int64), ("debug_barrier_extra", ctypes.c_int32),
                 ("sweep_kernel", ctypes.c_int32), ("record_trace", ctypes.c_int32),
-                ("schedule_delay", ctypes.c_int32), ("solo_width", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("schedule_delay", ctypes.c_int32), ("solo_width", ctypes.c_int32),
+                ("chunk_span", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 _lib = None

@@ -125,7 +125,7 @@ struct iso_graph {
     std::vector<uint32_t> h_down_off;
     std::vector<int32_t> h_down_src, h_bfs;
     struct CachedSchedule {
-        int vpb, narrow_width, sync_levels, delay;
+        int vpb, narrow_width, sync_levels, delay, chunk_span;
         std::shared_ptr<SweepSchedule> s;
     };
     std::vector<CachedSchedule> schedules;
@@ -152,6 +152,7 @@ struct iso_workspace {
     int solo_width = 0;          // TMA sweep: top levels up to this size run in one CTA (0: none)
     int solo_levels = 0;         // ... how many levels that is on this graph
     int sync_levels = 0;         // TMA sweep: leading levels swept level by level before the schedule
+    int chunk_span = 0;          // TMA sweep: largest BFS-rank span of a chunk (0: no limit)
     bool record_trace = false;
     long long* trace = nullptr;  // device [nsched + 1]
     std::vector<long long> h_trace;
@@ -264,16 +265,18 @@ int build_schedule(iso_workspace* ws) {
         static_assert(sizeof(SchedChunk) == 2 * sizeof(int4), "schedule record layout");
         std::shared_ptr<SweepSchedule> sc;
         for (auto& c : g->schedules)
-            if (c.vpb == ws->vpb && c.narrow_width == ws->narrow_width && c.sync_levels == sync && c.delay == delay)
+            if (c.vpb == ws->vpb && c.narrow_width == ws->narrow_width && c.sync_levels == sync && c.delay == delay &&
+                c.chunk_span == ws->chunk_span)
                 sc = c.s;
         if (!sc) {
             sc = std::make_shared<SweepSchedule>();
             if (iso_make_schedule(g->n, g->L, g->h_level_off.data(), g->h_down_off.data(), g->h_down_src.data(),
-                                  g->h_bfs.data(), ws->vpb, 31, ws->narrow_width, sync, delay, sc.get()) != 0) {
+                                  g->h_bfs.data(), ws->vpb, 31, ws->narrow_width, sync, delay, ws->chunk_span,
+                                  sc.get()) != 0) {
                 iso::set_error("workspace: could not build the sweep schedule");
                 return ISO_E_INVAL;
             }
-            g->schedules.push_back({ws->vpb, ws->narrow_width, sync, delay, sc});
+            g->schedules.push_back({ws->vpb, ws->narrow_width, sync, delay, ws->chunk_span, sc});
         }
         ws->Q = sc->Q;
         ws->sched_info = (int4*)ws->alloc(std::max<size_t>(sc->Q, 1) * sizeof(SchedChunk));
@@ -422,7 +425,7 @@ int check_opts(const iso_query_opts* o) {
     for (int r : o->reserved)
         if (r) { iso::set_error("iso_query_opts: reserved fields must be zero"); return ISO_E_INVAL; }
     if (o->threads_per_vertex < 0 || o->ctas_per_sm < 0 || o->fuse_width < -1 || o->barrier_timeout_ns < 0 ||
-        o->debug_barrier_extra < 0 || o->schedule_delay < 0 || o->solo_width < -1) {
+        o->debug_barrier_extra < 0 || o->schedule_delay < 0 || o->solo_width < -1 || o->chunk_span < 0) {
         iso::set_error("iso_query_opts: negative field");
         return ISO_E_INVAL;
     }
@@ -551,6 +554,7 @@ extern "C" int iso_workspace_create(iso_graph* g, int32_t lanes, const iso_query
     ws->record_trace = o.record_trace != 0 && ws->kernel == 1;
     ws->sched_delay = o.schedule_delay > 0 ? o.schedule_delay : 4 * ws->grid;
     ws->solo_width = o.solo_width < 0 ? 0 : (o.solo_width > 0 ? o.solo_width : kSoloWidth);
+    ws->chunk_span = o.chunk_span;
     ws->use_graph = opts ? opts->use_cuda_graph != 0 : false;
     if (opts && opts->barrier_timeout_ns) ws->timeout_ns = opts->barrier_timeout_ns;
     ws->bar_extra = opts ? opts->debug_barrier_extra : 0;
@@ -770,7 +774,8 @@ bool same_config(const iso_workspace* ws, const iso_query_opts& o) {
            ws->fuse_width == fuse && ws->use_graph == (o.use_cuda_graph != 0) && ws->timeout_ns == timeout &&
            ws->bar_extra == o.debug_barrier_extra && ws->record_trace == (o.record_trace != 0 && kernel == 1) &&
            ws->sched_delay == (o.schedule_delay > 0 ? o.schedule_delay : 4 * ws->g->num_sms * per_sm) &&
-           ws->solo_width == (o.solo_width < 0 ? 0 : (o.solo_width > 0 ? o.solo_width : kSoloWidth));
+           ws->solo_width == (o.solo_width < 0 ? 0 : (o.solo_width > 0 ? o.solo_width : kSoloWidth)) &&
+           ws->chunk_span == o.chunk_span;
 }
 }  // namespace
 

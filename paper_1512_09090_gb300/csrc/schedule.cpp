@@ -32,7 +32,7 @@
 
 int iso_make_schedule(int n, int L, const int32_t* level_off, const uint32_t* down_off, const int32_t* down_src,
                       const int32_t* bfs, int vpb, int narrow_chunk, int narrow_width, int sync_levels, int delay,
-                      SweepSchedule* out) {
+                      int chunk_span, SweepSchedule* out) {
     if (n <= 0 || L <= 0 || vpb <= 0 || narrow_chunk <= 0 || sync_levels < 0 || sync_levels > L) return -1;
     // chunks in level order
     std::vector<int32_t> cv0, cv1, clev, cmode;
@@ -41,11 +41,16 @@ int iso_make_schedule(int n, int L, const int32_t* level_off, const uint32_t* do
         const int lo = level_off[j], hi = level_off[j + 1];
         const int mode = narrow_width > 0 && hi - lo < narrow_width ? 1 : 0;
         const int per = mode ? narrow_chunk : vpb;
-        for (int b = lo; b < hi; b += per) {
+        for (int b = lo; b < hi;) {
+            // up to `per` vertices, and (chunk_span > 0) within chunk_span BFS
+            // ranks of the first: a sparse level's chunk then covers a small
+            // part of the map, so its rows are read again soon
+            int e = b + 1;
+            while (e < hi && e - b < per && (chunk_span <= 0 || (int64_t)bfs[e] - bfs[b] < chunk_span)) ++e;
             const int c = (int)cv0.size();
-            const int e = std::min(b + per, hi);
             cv0.push_back(b); cv1.push_back(e); clev.push_back(j); cmode.push_back(mode);
             for (int v = b; v < e; ++v) chunk_of[v] = c;
+            b = e;
         }
     }
     const int Q = (int)cv0.size();

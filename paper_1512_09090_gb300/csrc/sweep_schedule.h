@@ -28,7 +28,9 @@ struct SweepSchedule {
 // Builds the schedule for chunks of `vpb` vertices (levels narrower than
 // narrow_width: chunks of narrow_chunk vertices, a warp per vertex) of levels
 // sync_levels .. L-1; the levels above are swept before the schedule starts.
-// Returns 0, or -1 if the input is inconsistent.
+// chunk_span > 0 also ends a chunk where the BFS rank of its next vertex is
+// chunk_span or more above that of its first (bfs is non-decreasing within a
+// level).  Returns 0, or -1 if the input is inconsistent.
 int iso_make_schedule(int n, int L, const int32_t* level_off, const uint32_t* down_off, const int32_t* down_src,
                       const int32_t* bfs, int vpb, int narrow_chunk, int narrow_width, int sync_levels, int delay,
-                      SweepSchedule* out);
+                      int chunk_span, SweepSchedule* out);

@@ -147,6 +147,16 @@ def test_leading_level_phases(solo, fuse):
     check_batch(g, dg, srcs, taus, want_dist=True, solo_width=solo, fuse_width=fuse, sweep_kernel=1)
 
 
+@pytest.mark.parametrize("span", [512, 4096])
+def test_chunk_span_limit(span):
+    # chunks of sparse levels cut by BFS-rank span: many chunks smaller than
+    # the thread groups of a CTA
+    g, dg = dev_graph("grid1k")
+    srcs = synth.draw_sources(g, 16, 71)
+    taus = synth.draw_taus_uniform(16, 0, 60000, 72)
+    check_batch(g, dg, srcs, taus, want_dist=True, chunk_span=span, sweep_kernel=1)
+
+
 @pytest.mark.parametrize("solo", [-1, 124, 4000])
 def test_top_block_grid1k(solo):
     g, dg = dev_graph("grid1k")

@@ -8,7 +8,8 @@ dependency graph, and the dependency lists -- reduced by dropping lists that
 another dependency already implies -- must still imply every real dependency.
 A small C++ driver links schedule.cpp, builds schedules for random
 level-structured DAGs and checks exactly that, plus the record layout the
-kernel's bulk copies need (16-byte aligned, padded lists; even arc bases)."""
+kernel's bulk copies need (16-byte aligned, padded lists; even arc bases) and
+the optional limit on a chunk's BFS-rank span."""
 
 import os
 import shutil
@@ -33,7 +34,7 @@ DRIVER = textwrap.dedent(r"""
     }
 
     // one random hierarchy: level sizes, downward arcs from higher to lower levels
-    static int check(unsigned seed, int vpb, int narrow_width, int sync_levels, int delay) {
+    static int check(unsigned seed, int vpb, int narrow_width, int sync_levels, int delay, int span) {
         std::mt19937 rng(seed);
         const int L = 2 + (int)(rng() % 12);
         std::vector<int32_t> level_off(L + 1, 0);
@@ -60,7 +61,7 @@ DRIVER = textwrap.dedent(r"""
 
         SweepSchedule S;
         if (iso_make_schedule(n, L, level_off.data(), down_off.data(), down_src.data(), bfs.data(), vpb, 31,
-                              narrow_width, sync_levels, delay, &S) != 0)
+                              narrow_width, sync_levels, delay, span, &S) != 0)
             return fail("build", seed, 0);
         const int Q = S.Q;
         // every vertex below the synchronous levels in exactly one chunk; chunks within one level
@@ -75,6 +76,7 @@ DRIVER = textwrap.dedent(r"""
             for (int v = c.v0; v < c.v1; ++v) {
                 if (pos_of_v[v] != -1) return fail("vertex twice", v, q);
                 pos_of_v[v] = q;
+                if (span > 0 && bfs[v] - bfs[c.v0] >= span) return fail("chunk span", q, v);
             }
             if ((c.abase & 1) != 0 || (uint32_t)c.abase > down_off[c.v0]) return fail("arc base", q, c.abase);
             if ((uint32_t)(c.abase + c.na) != down_off[c.v1]) return fail("arc count", q, c.na);
@@ -117,10 +119,11 @@ DRIVER = textwrap.dedent(r"""
             for (int vpb : {1, 7, 64})
                 for (int nw : {0, 50})
                     for (int sync : {0, 2})
-                        for (int delay : {0, 3, 40}) {
-                            bad += check(seed, vpb, nw, sync, delay);
-                            ++runs;
-                        }
+                        for (int delay : {0, 3, 40})
+                            for (int span : {0, 1, 100}) {
+                                bad += check(seed, vpb, nw, sync, delay, span);
+                                ++runs;
+                            }
         std::printf("%d runs, %d failed\n", runs, bad);
         return bad ? 1 : 0;
     }
