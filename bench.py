@@ -36,17 +36,34 @@ WORKLOADS = {
     "grid18m_k16": dict(graph="grid18m", k=16, tau=("fixed", 36000)),
     # 18M-vertex graph, one source per launch
     "grid18m_k1": dict(graph="grid18m", k=1, tau=("uniform", 3600, 72000)),
+    # 18M-vertex graph, uneven limits, queries per sweep chosen by the autotuner among 16, 32, 64
+    "grid18m_kauto": dict(graph="grid18m", k=64, lanes=(16, 32, 64), tau=("uniform", 3600, 72000)),
     "grid4m_k64": dict(graph="grid4m", k=64, tau=("uniform", 3600, 72000)),
     "grid4m_k16": dict(graph="grid4m", k=16, tau=("fixed", 36000)),
     "grid1k_k1": dict(graph="grid1k", k=1, tau=("choice", (2000, 10000, 50000))),
+    # 64 x 64 grid (4,096 vertices), one query with limit 1,500
+    "grid64_k1": dict(graph="grid64", k=1, tau=("fixed", 1500)),
     "grid1k_k16": dict(graph="grid1k", k=16, tau=("choice", (2000, 10000, 50000))),
     "grid1k_k64": dict(graph="grid1k", k=64, tau=("uniform", 2000, 50000)),
 }
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one sweep launch
-# from one ncu capture per workload, with the hash of the sweep's sources that
-# capture ran; reported as the roofline's traffic only while the hash matches.
-SWEEP_TRAFFIC = {"grid18m_k64": ("6a8b1f134232b9de", 15_270_385_152 + 3_365_787_136)}
+# from one ncu capture per workload, with the hash of the sweep's sources and
+# the sweep options that capture ran; reported as the roofline's traffic only
+# while both match the run (else null).
+SWEEP_TRAFFIC = {}
 SWEEP_SOURCES = ("k_sweep_tma.cu", "iso_device.cuh", "schedule.cpp")
+# sweep options that change the kernel's memory traffic, with their defaults
+# (0 = the library's automatic choice)
+TRAFFIC_OPTS = ("threads_per_vertex", "schedule_delay", "chunk_span", "solo_width", "fuse_width", "ctas_per_sm",
+                "sweep_kernel")
+
+
+def lanes_class(k):
+    """Lanes of the sweep that serves k queries (the library rounds k up to 1, 4, 8, 16, 32 or 64)."""
+    for K in (1, 4, 8, 16, 32, 64):
+        if k <= K:
+            return K
+    return 64
 
 
 def max_over_ranks(x, dist=None, device="cpu"):
@@ -87,9 +104,18 @@ def sweep_source_hash():
     return h.hexdigest()[:16]
 
 
-def sweep_traffic(workload):
+def traffic_key(opts):
+    """The options of a run that decide the sweep's traffic (absent = 0 = automatic)."""
+    return {k: int(opts.get(k, 0)) for k in TRAFFIC_OPTS}
+
+
+def sweep_traffic(workload, opts):
+    """DRAM bytes of one sweep launch from the recorded ncu capture, or None
+    unless that capture ran the same sweep sources with the same options."""
     rec = SWEEP_TRAFFIC.get(workload)
-    return rec[1] if rec and rec[0] == sweep_source_hash() else None
+    if not rec or rec[0] != sweep_source_hash() or traffic_key(rec[1]) != traffic_key(opts):
+        return None
+    return rec[2]
 
 
 METRIC = "isochrone queries/s on 18M-vertex graph (1 GB300); sweep HBM GB/s vs peak; p99 ms"
@@ -117,11 +143,22 @@ def load_graph_and_ch(name):
     return chcache.workload_graph_and_ch(name, log=log)
 
 
+def sweep_bytes_scope(A, k):
+    """Algorithmic bytes of one sweep of k lanes as the measurement scope counts
+    them: B = 4(n+1) offsets + 8 m_down arcs + 4kn label writes + 4kn label
+    reads + 4(L+1) level table."""
+    n = A["perm"].shape[0]
+    m_down = int(A["down_src"].shape[0])
+    levels = int(A["level_off"].shape[0])  # L + 1
+    return dict(offsets=4 * (n + 1), arcs=8 * m_down, d_write=4 * k * n, d_read=4 * k * n, levels=4 * levels)
+
+
 def sweep_bytes(A, k, write_all=False):
-    """Algorithmic bytes one sweep of k lanes must move: the CSR offsets and
-    every downward arc once, every stored label row written once, every row
-    that is the source of a downward arc read once, the in-range masks written,
-    the upward-label flags read and the level table."""
+    """Algorithmic bytes of this design's sweep of k lanes (a tighter count than
+    sweep_bytes_scope): the CSR offsets and every downward arc once, every
+    stored label row written once (the lowest level's rows are not stored),
+    every row that is the source of a downward arc read once, the in-range
+    masks written, the upward-label flags read and the level table."""
     n = A["perm"].shape[0]
     lo = A["level_off"]
     n_low = int(lo[-1] - lo[-2])                 # lowest level: rows not stored
@@ -315,11 +352,15 @@ def main():
     tuned = None
     if not args.no_autotune and not (args.tpv or args.delay or args.sweep_kernel):
         from paper_1512_09090_gb300 import autotune
-        ts = synth.draw_sources(g, 4 * k, 777)
-        tt = draw_taus(spec["tau"], 4 * k, 778)
-        tuned = autotune.tune(dg, ts, tt, lanes_choices=(k,), reps=4, budget_s=90.0,
+        # the configurations fix the queries per sweep (k) except where the
+        # workload lists lane choices; every other axis is tuned
+        lanes_choices = tuple(spec.get("lanes", (k,)))
+        ts = synth.draw_sources(g, 8 * max(lanes_choices), 777)
+        tt = draw_taus(spec["tau"], 8 * max(lanes_choices), 778)
+        tuned = autotune.tune(dg, ts, tt, lanes_choices=lanes_choices, reps=8, budget_s=150.0,
                               cache_path=os.path.join(CACHE, "autotune.json"), log=log)
-        for key in ("threads_per_vertex", "schedule_delay"):
+        k = int(tuned["lanes"])
+        for key in autotune.TUNED_KEYS:
             if key in tuned:
                 opts[key] = tuned[key]
     for flag, key in ((args.tpv, "threads_per_vertex"), (args.delay, "schedule_delay"),
@@ -463,14 +504,20 @@ def main():
         if dist:
             dist.destroy_process_group()
         return
-    bb = sweep_bytes(A, k)
-    alg = sum(bb.values())
+    K = lanes_class(k)
+    alg = sum(sweep_bytes_scope(A, K).values())
+    alg_design = sum(sweep_bytes(A, K).values())
     sw = statistics.mean(sweep_ms)
     peak, src = peaks()
     achieved = alg / (sw / 1e3) / 1e9
+    traffic = sweep_traffic(args.workload, opts)
+    info = ws.sweep_info()
+    kern = f"k_sweep_tma<{K}>" if not info["core_levels"] else f"k_core + k_sweep_tma<{K}>"
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": sweep_traffic(args.workload), "kernel": "k_sweep",
-            "alg_bytes_per_launch": alg, "peak_source": src, "sweep_ms": round(sw, 4)}
+            "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": kern,
+            "alg_bytes_per_launch": alg, "alg_bytes_design": alg_design,
+            "traffic_over_alg": None if traffic is None else round(traffic / alg, 3),
+            "peak_source": src, "sweep_ms": round(sw, 4), "lanes_per_launch": K}
     lat = sorted(pipelined["latency_ms"])
     line = {"metric": METRIC, "value": round(value, 2), "unit": "queries/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(el_ms / args.steps, 4), "higher_is_better": True,
@@ -486,7 +533,8 @@ def main():
             "phases_ms": {key: round(statistics.mean(p[key] for p in phases), 4) for key in phases[0]},
             "serving": serving_stats,
             "autotune": None if tuned is None else {kk: v for kk, v in tuned.items() if kk != "tried"},
-            "gpu_launches": 4 * args.steps, "e2e": e2e}
+            "gpu_launches": (5 if info["core_levels"] else 4) * args.steps, "e2e": e2e,
+            "sweep_shape": info}
     clocks = clk.summary()
     if clocks:
         line["clocks"] = clocks

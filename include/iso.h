@@ -125,8 +125,9 @@ typedef struct {
     void* ctx;
 } iso_alloc;
 
-/* Copy the CH to the current CUDA device (sweep-ordered CSRs, Section 2's
- * "linear sweep over an edge array").  alloc may be NULL, in which case
+/* Copy the CH to the current CUDA device as sweep-ordered CSRs (Section 2:
+ * vertices are renumbered so that the scan reads one array of arcs from front
+ * to back).  alloc may be NULL, in which case
  * cudaMalloc/cudaFree are used.  The iso_ch may be freed
  * afterwards.  Errors: ISO_E_INVAL, ISO_E_NOMEM, ISO_E_CUDA, ISO_E_NODEV. */
 int iso_upload_graph(const iso_ch* ch, const iso_alloc* alloc, void* stream, iso_graph** out);
@@ -162,7 +163,16 @@ typedef struct {
     int32_t chunk_span;         /* TMA-staged sweep: a chunk also ends where the BFS rank of its next
                                    vertex is this far or more above its first one's, so that chunks
                                    of sparse levels cover small parts of the map; 0 = no limit */
-    int32_t reserved[2];        /* must be zero */
+    int32_t core_vertices;      /* TMA-staged sweep: the top level blocks of the hierarchy, as long as
+                                   they hold at most this many vertices in total, are swept for each
+                                   lane by one CTA with the lane's labels in shared memory (Section 5's
+                                   small top graph swept first); 0 = auto (the most that fit, 53,248),
+                                   -1 = never */
+    int32_t debug_stage_arcs;   /* testing only (TMA-staged sweep): stage at most this many arcs per
+                                   chunk in shared memory (0 = the buffer size, 3,072); chunks with
+                                   more read their arcs from global memory */
+    int32_t debug_stage_deps;   /* testing only: likewise for dependency-list entries (0 = 128) */
+    int32_t reserved[1];        /* must be zero */
 } iso_query_opts;
 
 /* Answer k isochrone queries (source sources[i], limit taus[i]) in sweeps of
@@ -197,6 +207,17 @@ int iso_submit(iso_workspace* ws, int32_t k, const int32_t* sources, const int32
  * does (same layout, overflow and distance conventions). */
 int iso_collect(iso_workspace* ws, int64_t* out_offsets, int32_t* out_arcs, int64_t cap,
                 int32_t* out_dist);
+/* Vertices in range (Section 3 names this as another output the problem can
+ * ask for) of the batch last collected on ws: for query i, bit v of the
+ * bitset out_bits[i * words_per_query .. + ceil(n/32)) (32-bit words, bit v
+ * = bit v % 32 of word v / 32, v an original vertex id) is set iff
+ * d(sources[i], v) <= taus[i].  out_bits is host or device memory (detected);
+ * words_per_query >= ceil(n/32); words beyond ceil(n/32) are not written.
+ * Valid after iso_collect returned ISO_OK or ISO_E_OVERFLOW and before the
+ * next iso_submit on ws; synchronizes the workspace's stream.  Errors:
+ * ISO_E_INVAL (nothing collected, NULL or short buffer), ISO_E_NOMEM,
+ * ISO_E_CUDA. */
+int iso_collect_range(iso_workspace* ws, uint32_t* out_bits, int64_t words_per_query);
 /* Per-phase device times of the last collected batch in milliseconds:
  * [0] upward search, [1] sweep, [2] emission, [3] sort + gather. */
 int iso_workspace_timings(const iso_workspace* ws, float* ms4);
@@ -210,6 +231,24 @@ int iso_workspace_timings(const iso_workspace* ws, float* ms4);
  * the label rows).  Returns L+1 (at most cap entries are written) or -1 on
  * error. */
 int32_t iso_workspace_trace(const iso_workspace* ws, int32_t* steps4, int64_t* ns, int32_t cap);
+/* Shape of a workspace's sweep on its graph (TMA-staged sweep; zeros for the
+ * plain one): how the level blocks are split between the phases and the chunk
+ * schedule's extremes against the shared-memory staging limits. */
+typedef struct {
+    int32_t levels;              /* level blocks L */
+    int32_t core_levels;         /* blocks 0 .. core_levels-1: per-lane core */
+    int32_t core_vertices;       /* vertices in those blocks */
+    int32_t solo_levels;         /* blocks core_levels .. solo_levels-1: CTA 0 alone */
+    int32_t sync_levels;         /* blocks solo_levels .. sync_levels-1: grid-synchronous */
+    int32_t chunks;              /* chunks of the schedule (blocks sync_levels .. L-1) */
+    int32_t max_chunk_arcs;      /* largest arc block of a chunk */
+    int32_t max_chunk_deps;      /* longest dependency list of a chunk */
+    int32_t chunks_over_arc_cap; /* chunks whose arcs are read from global memory */
+    int32_t chunks_over_dep_cap; /* chunks whose dependency list is checked in global memory */
+    int32_t arc_cap, dep_cap;    /* staging limits in force */
+    int32_t reserved[4];
+} iso_sweep_info;
+int iso_workspace_sweep_info(const iso_workspace* ws, iso_sweep_info* out);
 void iso_free_workspace(iso_workspace* ws);
 
 /* ---------------------------------------------------------------------------
@@ -227,11 +266,14 @@ void iso_free_workspace(iso_workspace* ws);
  * ISO_NOALLOC_MAX_QUERIES, a graph of at most ISO_NOALLOC_MAX_VERTICES vertices
  * and 4096 CH levels, at most ISO_NOALLOC_MAX_ARCS isochrone edges and 8192
  * upward-search vertices per query.  Inputs, outputs, overflow and errors are
- * as for iso_query (without out_dist).  The first call on each device looks up
+ * as for iso_query (without out_dist).  g must live on the current device
+ * (ISO_E_INVAL otherwise).  The first call on each device looks up
  * the array's device address, so make it before any stream capture on that
  * device.  All calls share the array: calls that overlap on the GPU (two
  * streams or two host threads at once) race and must be serialised by the
- * caller.  The call synchronizes `stream` before returning.
+ * caller.  The call synchronizes `stream` before returning, on failure too
+ * once anything was enqueued, so a failed call never leaves work running on
+ * the array.
  * ------------------------------------------------------------------------- */
 #define ISO_NOALLOC_MAX_VERTICES (1 << 20)
 #define ISO_NOALLOC_MAX_QUERIES 4

@@ -66,7 +66,19 @@ class QueryOpts(ctypes.Structure):
                 ("barrier_timeout_ns", ctypes.c_int64), ("debug_barrier_extra", ctypes.c_int32),
                 ("sweep_kernel", ctypes.c_int32), ("record_trace", ctypes.c_int32),
                 ("schedule_delay", ctypes.c_int32), ("solo_width", ctypes.c_int32),
-                ("chunk_span", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("chunk_span", ctypes.c_int32), ("core_vertices", ctypes.c_int32),
+                ("debug_stage_arcs", ctypes.c_int32), ("debug_stage_deps", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
+
+
+class SweepInfo(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int32) for k in ("levels", "core_levels", "core_vertices", "solo_levels",
+                                              "sync_levels", "chunks", "max_chunk_arcs", "max_chunk_deps",
+                                              "chunks_over_arc_cap", "chunks_over_dep_cap", "arc_cap",
+                                              "dep_cap")] + [("reserved", ctypes.c_int32 * 4)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
 _lib = None
@@ -91,6 +103,8 @@ EXPORTS = {
     "iso_free_workspace": (None, [VP]),
     "iso_query_noalloc": (I32, [VP, I32, VP, VP, VP, VP, I64, VP]),
     "iso_workspace_trace": (I32, [VP, VP, VP, I32]),
+    "iso_workspace_sweep_info": (I32, [VP, VP]),
+    "iso_collect_range": (I32, [VP, VP, I64]),
     "iso_last_error": (ctypes.c_char_p, []),
     "iso_version": (ctypes.c_char_p, []),
 }
@@ -362,6 +376,24 @@ class Workspace:
         ns = np.zeros(max(cnt, 1), np.int64)
         lib().iso_workspace_trace(self._h, steps.ctypes.data, ns.ctypes.data, cnt)
         return steps[:cnt], ns[:cnt]
+
+    def collect_range(self, out_bits=None):
+        """Vertices in range of the last collected batch (iso_collect_range):
+        uint32 bitsets, shape (k, ceil(n/32)), bit v of row i set iff original
+        vertex v is within query i's limit.  out_bits: optional caller buffer
+        (numpy or torch CUDA tensor) of that shape."""
+        words = (self.g.n + 31) // 32
+        if out_bits is None:
+            out_bits = np.zeros((self.k, words), dtype=np.uint32)
+        per = int(out_bits.shape[1]) if len(out_bits.shape) == 2 else words
+        _check(lib().iso_collect_range(self._h, _ptr(out_bits), per))
+        return out_bits
+
+    def sweep_info(self) -> dict:
+        """How the sweep splits the levels and the schedule's extremes (iso_workspace_sweep_info)."""
+        info = SweepInfo()
+        _check(lib().iso_workspace_sweep_info(self._h, ctypes.byref(info)))
+        return info.as_dict()
 
     def timings(self):
         t = (ctypes.c_float * 4)()

@@ -10,6 +10,7 @@
 
 struct iso_graph_view {
     int n, L, tau_max, num_sms;
+    int device;  // CUDA device the graph was uploaded to
     int64_t m;
     const uint32_t *down_off, *up_off, *orig_off;
     const int2 *down_arc, *up_arc;

@@ -82,6 +82,13 @@ int lanes_class(int k) {
 
 int default_tpv(int K) { return K <= 8 ? 1 : K / 8; }
 
+// Largest per-lane core (vertices) that options o allow on a graph of n vertices.
+int core_limit_of(const iso_query_opts& o, int n) {
+    if (o.core_vertices < 0) return 0;
+    const int lim = o.core_vertices > 0 ? std::min(o.core_vertices, kCoreMaxVertices) : kCoreMaxVertices;
+    return std::min(lim, n);
+}
+
 // Sweep kernel, threads per vertex, CTAs per SM and vertices per CTA batch that
 // options o select for K lanes.  Returns false if the combination is unsupported.
 bool sweep_shape(int K, const iso_query_opts& o, int* kernel, int* tpv, int* occ, int* vpb) {
@@ -117,6 +124,12 @@ struct iso_graph {
     int32_t* orig_head = nullptr;   // heads as sweep positions
     int32_t* orig_id = nullptr;     // input arc ids
     int32_t* emit_tail = nullptr;   // [n] sweep position of the tail at each emission index
+    // per-lane core of the TMA sweep: downward arcs into the first
+    // core_cap_n sweep positions packed as {src | head << 16, len}, and the
+    // first downward arc of every level block
+    uint2* core_arc = nullptr;
+    uint32_t* level_arc = nullptr;
+    int core_cap_n = 0;
     int32_t* perm = nullptr;
     int32_t* pos = nullptr;
     int32_t* level_off = nullptr;
@@ -153,6 +166,10 @@ struct iso_workspace {
     int solo_levels = 0;         // ... how many levels that is on this graph
     int sync_levels = 0;         // TMA sweep: leading levels swept level by level before the schedule
     int chunk_span = 0;          // TMA sweep: largest BFS-rank span of a chunk (0: no limit)
+    int core_limit = 0;          // TMA sweep: largest per-lane core (vertices; 0: none)
+    int core_levels = 0, core_n = 0;  // ... the level blocks and vertices it covers on this graph
+    int stage_arc_cap = 0, stage_pred_cap = 0;  // testing: lower staging limits (0: buffer sizes)
+    iso_sweep_info info{};       // the sweep's shape (iso_workspace_sweep_info)
     bool record_trace = false;
     long long* trace = nullptr;  // device [nsched + 1]
     std::vector<long long> h_trace;
@@ -172,6 +189,7 @@ struct iso_workspace {
     int32_t* done = nullptr;       // [Q] zeroed per batch
     int Q = 0;
     unsigned long long* upmask = nullptr;  // [n] TMA sweep: lanes with upward labels
+    uint32_t* core_out = nullptr;  // [K * core_n] TMA sweep: the per-lane core's labels, lane-major
     int vpb = 0;
     int2* pairs = nullptr;
     uint32_t* gtab = nullptr;
@@ -184,6 +202,8 @@ struct iso_workspace {
     int4* sched = nullptr;
     int nsched = 0;
     int32_t* dist = nullptr;     // [K * n] labels, query-major, original vertex order
+    uint32_t* range = nullptr;   // [K * ceil(n/32)] vertices-in-range bitsets (iso_collect_range)
+    bool collected = false;      // the last batch was collected successfully
     // pinned host mirrors
     int32_t* h_io = nullptr;     // src[K], tau[K]
     int32_t* h_ctl = nullptr;    // ctl after the last batch
@@ -254,8 +274,14 @@ int build_schedule(iso_workspace* ws) {
         // The leading levels sweep level by level before the schedule: those
         // with at most solo_width vertices in CTA 0 alone, the following ones
         // narrower than narrow_width in all CTAs with a grid barrier per level.
-        int solo = 0;
-        while (ws->solo_width > 0 && solo < g->L &&
+        // The per-lane core: the longest run of top level blocks whose vertices
+        // fit core_limit (it replaces the CTA-0-alone levels).
+        int core = 0;
+        while (core < g->L && core < kCoreMaxLevels && g->h_level_off[core + 1] <= ws->core_limit) ++core;
+        ws->core_levels = core;
+        ws->core_n = g->h_level_off[core];
+        int solo = core;
+        while (core == 0 && ws->solo_width > 0 && solo < g->L &&
                g->h_level_off[solo + 1] - g->h_level_off[solo] <= ws->solo_width)
             ++solo;
         int sync = solo;
@@ -279,6 +305,27 @@ int build_schedule(iso_workspace* ws) {
             g->schedules.push_back({ws->vpb, ws->narrow_width, sync, delay, ws->chunk_span, sc});
         }
         ws->Q = sc->Q;
+        {
+            iso_sweep_info& in = ws->info;
+            in.levels = g->L;
+            in.core_levels = core;
+            in.core_vertices = ws->core_n;
+            in.solo_levels = solo;
+            in.sync_levels = sync;
+            in.chunks = sc->Q;
+            int acap = 0, dcap = 0;
+            iso_sweep_tma_stage_caps(&acap, &dcap);
+            if (ws->stage_arc_cap > 0 && ws->stage_arc_cap < acap) acap = ws->stage_arc_cap;
+            if (ws->stage_pred_cap > 0 && ws->stage_pred_cap < dcap) dcap = ws->stage_pred_cap;
+            in.arc_cap = acap;
+            in.dep_cap = dcap;
+            for (const SchedChunk& c : sc->info) {
+                in.max_chunk_arcs = std::max(in.max_chunk_arcs, c.na);
+                in.max_chunk_deps = std::max(in.max_chunk_deps, c.np);
+                in.chunks_over_arc_cap += c.na > acap;
+                in.chunks_over_dep_cap += c.np > dcap;
+            }
+        }
         ws->sched_info = (int4*)ws->alloc(std::max<size_t>(sc->Q, 1) * sizeof(SchedChunk));
         ws->pred = (int32_t*)ws->alloc(sc->pred.size() * 4);
         ws->done = (int32_t*)ws->alloc(std::max<size_t>(sc->Q, 1) * 4);
@@ -332,6 +379,7 @@ int enqueue(iso_workspace* ws, bool want_dist, bool capturing) {
     up.pairs = ws->pairs; up.cnt = ws->upcnt(); up.gtab = ws->gtab; up.status = ws->status();
     up.n = g->n; up.cap = ws->gcap; up.gcap = ws->gcap; up.tau_max = g->tau_max;
     up.direct = ws->kernel == 1 ? 1 : 0;
+    up.core_n = ws->kernel == 1 ? ws->core_n : 0;
     up.K = K; up.d = ws->d; up.upmask = ws->upmask; up.upflag = ws->upflag;
     ISO_CK(iso_launch_upward(up, K, s));
     ISO_CK(record(ws->ev[1], s, capturing));
@@ -350,6 +398,14 @@ int enqueue(iso_workspace* ws, bool want_dist, bool capturing) {
     sw.sync_levels = ws->sync_levels;
     sw.Q = ws->Q;
     sw.upmask = ws->upmask;
+    sw.core_levels = ws->core_levels;
+    sw.core_n = ws->core_n;
+    sw.core_arc = g->core_arc;
+    sw.level_arc = g->level_arc;
+    sw.core_out = ws->core_out;
+    sw.stage_arc_cap = ws->stage_arc_cap;
+    sw.stage_pred_cap = ws->stage_pred_cap;
+    if (ws->kernel == 1 && ws->core_levels > 0) ISO_CK(iso_launch_core(sw, K, s));
     if (ws->kernel == 1) ISO_CK(iso_launch_sweep_tma(sw, K, ws->tpv, ws->grid, s));
     else ISO_CK(iso_launch_sweep(sw, K, ws->tpv, ws->grid, s));
     ISO_CK(record(ws->ev[2], s, capturing));
@@ -425,7 +481,8 @@ int check_opts(const iso_query_opts* o) {
     for (int r : o->reserved)
         if (r) { iso::set_error("iso_query_opts: reserved fields must be zero"); return ISO_E_INVAL; }
     if (o->threads_per_vertex < 0 || o->ctas_per_sm < 0 || o->fuse_width < -1 || o->barrier_timeout_ns < 0 ||
-        o->debug_barrier_extra < 0 || o->schedule_delay < 0 || o->solo_width < -1 || o->chunk_span < 0) {
+        o->debug_barrier_extra < 0 || o->schedule_delay < 0 || o->solo_width < -1 || o->chunk_span < 0 ||
+        o->core_vertices < -1 || o->debug_stage_arcs < 0 || o->debug_stage_deps < 0) {
         iso::set_error("iso_query_opts: negative field");
         return ISO_E_INVAL;
     }
@@ -466,6 +523,20 @@ extern "C" int iso_upload_graph(const iso_ch* ch, const iso_alloc* alloc, void* 
     arcs[arcs.size() - 1] = arcs[arcs.size() - 2] = make_int2(0, 0);
     if ((rc = g->upload(&g->down_off, off32.data(), n + 5)) || (rc = g->upload(&g->down_arc, arcs.data(), arcs.size()))) {
         free_all(); return rc;
+    }
+    {
+        g->core_cap_n = (int)std::min<size_t>(n, (size_t)kCoreMaxVertices);
+        const uint32_t na = off32[g->core_cap_n];
+        std::vector<uint2> ca(std::max<uint32_t>(na, 1u), make_uint2(0u, 0u));
+        for (int v = 0; v < g->core_cap_n; ++v)
+            for (uint32_t a = off32[v]; a < off32[v + 1]; ++a)
+                ca[a] = make_uint2((uint32_t)ch->down_src[a] | ((uint32_t)v << 16), (uint32_t)ch->down_w[a]);
+        std::vector<uint32_t> la(ch->level_off.size());
+        for (size_t j = 0; j < la.size(); ++j) la[j] = off32[ch->level_off[j]];
+        if ((rc = g->upload(&g->core_arc, ca.data(), ca.size())) || (rc = g->upload(&g->level_arc, la.data(), la.size()))) {
+            free_all(); return rc;
+        }
+        ISO_CK(cudaStreamSynchronize(g->stream));
     }
     ISO_CK(cudaStreamSynchronize(g->stream));
     try {
@@ -555,6 +626,9 @@ extern "C" int iso_workspace_create(iso_graph* g, int32_t lanes, const iso_query
     ws->sched_delay = o.schedule_delay > 0 ? o.schedule_delay : 4 * ws->grid;
     ws->solo_width = o.solo_width < 0 ? 0 : (o.solo_width > 0 ? o.solo_width : kSoloWidth);
     ws->chunk_span = o.chunk_span;
+    ws->core_limit = core_limit_of(o, g->n);
+    ws->stage_arc_cap = o.debug_stage_arcs;
+    ws->stage_pred_cap = o.debug_stage_deps;
     ws->use_graph = opts ? opts->use_cuda_graph != 0 : false;
     if (opts && opts->barrier_timeout_ns) ws->timeout_ns = opts->barrier_timeout_ns;
     ws->bar_extra = opts ? opts->debug_barrier_extra : 0;
@@ -592,6 +666,10 @@ extern "C" int iso_workspace_create(iso_graph* g, int32_t lanes, const iso_query
     }
     for (auto& e : ws->ev)
         if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); iso::set_error("iso_workspace_create: event"); return fail(ISO_E_CUDA); }
+    if (ws->kernel == 1 && ws->core_levels > 0) {
+        ws->core_out = (uint32_t*)ws->alloc(K * (size_t)ws->core_n * 4);
+        if (!ws->core_out) { iso::set_error("iso_workspace_create: device allocation failed"); return fail(ISO_E_NOMEM); }
+    }
     if (ws->kernel == 1) {
         ws->upmask = (unsigned long long*)ws->alloc(n * 8);
         if (!ws->upmask) { iso::set_error("iso_workspace_create: device allocation failed"); return fail(ISO_E_NOMEM); }
@@ -657,6 +735,7 @@ int submit_impl(iso_workspace* ws, int32_t k, const int32_t* sources, const int3
     if (dev_t && k) ISO_CK(cudaMemcpyAsync(ws->io + K, taus, (size_t)k * 4, cudaMemcpyDeviceToDevice, stream));
     ws->k = k;
     ws->want_dist = want_dist;
+    ws->collected = false;
     int rc = launch_batch(ws, want_dist);
     if (rc) return rc;
     ws->submitted = true;
@@ -716,7 +795,37 @@ int collect_impl(iso_workspace* ws, int64_t* out_offsets, int32_t* out_arcs, int
     if (out_dist && rc == ISO_OK)
         if (int r2 = copy_out(out_dist, ws->dist, (size_t)ws->k * ws->g->n * 4, s)) return r2;
     ISO_CK(cudaStreamSynchronize(s));
+    ws->collected = rc == ISO_OK || rc == ISO_E_OVERFLOW;
     return rc;
+}
+
+int range_impl(iso_workspace* ws, uint32_t* out_bits, int64_t words) {
+    if (!ws->collected) { iso::set_error("iso_collect_range: no collected batch"); return ISO_E_INVAL; }
+    const int n = ws->g->n;
+    const int64_t need = ((int64_t)n + 31) / 32;
+    if (!out_bits && ws->k > 0) { iso::set_error("iso_collect_range: out_bits is NULL"); return ISO_E_INVAL; }
+    if (words < need) { iso::set_error("iso_collect_range: %lld words per query, %lld needed", (long long)words, (long long)need); return ISO_E_INVAL; }
+    if (ws->k == 0) return ISO_OK;
+    cudaStream_t s = ws->stream;
+    const bool dev = is_device_ptr(out_bits);
+    uint32_t* dst = out_bits;
+    if (!dev) {
+        if (!ws->range) {
+            ws->range = (uint32_t*)ws->alloc((size_t)ws->K * need * 4);
+            if (!ws->range) { iso::set_error("iso_collect_range: device allocation failed"); return ISO_E_NOMEM; }
+        }
+        dst = ws->range;
+    }
+    RangeParams rp{};
+    rp.pos = ws->g->pos; rp.mask = ws->mask; rp.out = dst; rp.words = dev ? words : need; rp.n = n; rp.k = ws->k;
+    ISO_CK(iso_launch_range(rp, ws->K, s));
+    if (!dev) {
+        // query i's bitset to out_bits[i * words], words beyond the need untouched
+        ISO_CK(cudaMemcpy2DAsync(out_bits, (size_t)words * 4, dst, (size_t)need * 4, (size_t)need * 4, ws->k,
+                                 cudaMemcpyDeviceToHost, s));
+    }
+    ISO_CK(cudaStreamSynchronize(s));
+    return ISO_OK;
 }
 }  // namespace
 
@@ -733,6 +842,12 @@ extern "C" int iso_collect(iso_workspace* ws, int64_t* out_offsets, int32_t* out
     iso::clear_error();
     if (!ws) { iso::set_error("iso_collect: NULL workspace"); return ISO_E_INVAL; }
     return collect_impl(ws, out_offsets, out_arcs, cap, out_dist);
+}
+
+extern "C" int iso_collect_range(iso_workspace* ws, uint32_t* out_bits, int64_t words_per_query) {
+    iso::clear_error();
+    if (!ws) { iso::set_error("iso_collect_range: NULL workspace"); return ISO_E_INVAL; }
+    return range_impl(ws, out_bits, words_per_query);
 }
 
 extern "C" int32_t iso_workspace_trace(const iso_workspace* ws, int32_t* steps4, int64_t* ns, int32_t cap) {
@@ -756,6 +871,13 @@ extern "C" int32_t iso_workspace_trace(const iso_workspace* ws, int32_t* steps4,
     return L + 1;
 }
 
+extern "C" int iso_workspace_sweep_info(const iso_workspace* ws, iso_sweep_info* out) {
+    iso::clear_error();
+    if (!ws || !out) { iso::set_error("iso_workspace_sweep_info: NULL argument"); return ISO_E_INVAL; }
+    *out = ws->info;
+    return ISO_OK;
+}
+
 extern "C" int iso_workspace_timings(const iso_workspace* ws, float* ms4) {
     if (!ws || !ms4) return ISO_E_INVAL;
     std::memcpy(ms4, ws->phase_ms, sizeof(ws->phase_ms));
@@ -775,7 +897,8 @@ bool same_config(const iso_workspace* ws, const iso_query_opts& o) {
            ws->bar_extra == o.debug_barrier_extra && ws->record_trace == (o.record_trace != 0 && kernel == 1) &&
            ws->sched_delay == (o.schedule_delay > 0 ? o.schedule_delay : 4 * ws->g->num_sms * per_sm) &&
            ws->solo_width == (o.solo_width < 0 ? 0 : (o.solo_width > 0 ? o.solo_width : kSoloWidth)) &&
-           ws->chunk_span == o.chunk_span;
+           ws->chunk_span == o.chunk_span && ws->core_limit == core_limit_of(o, ws->g->n) &&
+           ws->stage_arc_cap == o.debug_stage_arcs && ws->stage_pred_cap == o.debug_stage_deps;
 }
 }  // namespace
 
@@ -834,6 +957,7 @@ extern "C" int iso_query(iso_graph* g, int32_t k, const int32_t* sources, const 
 int iso_graph_view_of(const iso_graph* g, iso_graph_view* v) {
     if (!g || !v) return ISO_E_INVAL;
     v->n = g->n; v->L = g->L; v->tau_max = g->tau_max; v->num_sms = g->num_sms; v->m = g->m;
+    v->device = g->device;
     v->down_off = g->down_off; v->up_off = g->up_off; v->orig_off = g->orig_off;
     v->down_arc = g->down_arc; v->up_arc = g->up_arc;
     v->orig_head = g->orig_head; v->orig_id = g->orig_id; v->pos = g->pos; v->level_off = g->level_off;

@@ -13,9 +13,17 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace isod {
 
 constexpr uint32_t kInf = 0x7FFFFFFFu;
+
+// Per-lane core of the TMA-staged sweep: at most this many vertices (one
+// lane's labels in a CTA's shared memory; heads and sources fit 16 bits) in at
+// most this many level blocks.
+constexpr int kCoreMaxVertices = 53248;
+constexpr int kCoreMaxLevels = 1023;
 
 // Device status word values (status[0]); the host maps them to ISO_E_*.
 enum : int {
@@ -44,8 +52,10 @@ struct UpParams {
     int gcap;                 // power of two
     int tau_max;
     // direct != 0: instead of pairs, write every label into its row slot d[v*K + lane],
-    // set bit lane of upmask[v] and upflag[v] (the TMA sweep reads them there)
+    // set bit lane of upmask[v] and upflag[v] (the TMA sweep reads them there);
+    // labels of vertices below core_n still go to pairs (cnt[lane] of them)
     int direct;
+    int core_n;
     int K;
     uint32_t* d;
     unsigned long long* upmask;
@@ -80,6 +90,16 @@ struct SweepParams {
     int sync_levels;           // then levels .. sync_levels-1 by all CTAs, a grid barrier per level
     int Q;
     unsigned long long* upmask;// [n] lanes with an upward label (TMA kernel)
+    // TMA kernel, per-lane core: levels 0 .. core_levels-1 (vertices [0, core_n))
+    // are swept by CTA i for lane i alone, labels in shared memory, starting
+    // from the lane's upward labels in pairs[i*cap .. + cnt[i]]
+    int core_levels, core_n;
+    const uint2* core_arc;     // downward arcs into [0, core_n): {src | head << 16, len}
+    const uint32_t* level_arc; // [L+1] first downward arc of each level block
+    uint32_t* core_out;        // [K * core_n] final core labels, lane-major (k_core -> sweep)
+    // testing: stage at most this many arcs / dependency-list entries per chunk
+    // (0 = the buffer sizes); larger chunks take the global-memory paths
+    int stage_arc_cap, stage_pred_cap;
 };
 
 struct EmitParams {
@@ -105,6 +125,14 @@ struct GatherParams {
     const int32_t* status;     // batch status: nothing is written once it is not kStOk
 };
 
+struct RangeParams {
+    const int32_t* pos;        // [n] original id -> sweep position
+    const void* mask;          // [n] K-bit in-range words (sweep order)
+    uint32_t* out;             // [k * words] bitsets over original ids, query-major
+    int64_t words;             // 32-bit words per query (>= ceil(n / 32))
+    int n, k;
+};
+
 struct DistParams {
     const uint32_t* d;
     const int32_t* perm;
@@ -120,6 +148,22 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 }  // namespace isod
 
+// Raises kernel f's dynamic shared-memory limit to `bytes` on the current
+// device.  Function attributes belong to a device's context, so this is done
+// once per device: bit d of `done` records device d (devices beyond 63 set it
+// on every call).  Concurrent first calls may both set it, which is harmless.
+template <class F>
+cudaError_t iso_smem_attr_once(F* f, int bytes, std::atomic<unsigned long long>& done) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_release);
+    return e;
+}
+
 // Launchers (one translation unit each); return the launch's cudaError_t.
 cudaError_t iso_launch_upward(const isod::UpParams& p, int K, cudaStream_t s);
 size_t iso_upward_table_words(size_t gcap);  // 32-bit words of one lane's global table
@@ -127,8 +171,12 @@ cudaError_t iso_launch_sweep(const isod::SweepParams& p, int K, int tpv, int gri
 int iso_sweep_occupancy(int K, int tpv, int* block);
 bool iso_sweep_supported(int K, int tpv);
 cudaError_t iso_launch_sweep_tma(const isod::SweepParams& p, int K, int tpv, int grid, cudaStream_t s);
+// Per-lane core (k_core.cu): K CTAs; runs before iso_launch_sweep_tma when p.core_levels > 0.
+cudaError_t iso_launch_core(const isod::SweepParams& p, int K, cudaStream_t s);
 int iso_sweep_tma_occupancy(int K, int tpv, int* block, int* vpb);
 bool iso_sweep_tma_supported(int K, int tpv);
+void iso_sweep_tma_stage_caps(int* arcs, int* deps);  // stage buffer sizes (arcs, dependency entries)
 cudaError_t iso_launch_emit(const isod::EmitParams& p, int K, int grid, cudaStream_t s);
 cudaError_t iso_launch_sort_gather(const isod::GatherParams& p, int K, cudaStream_t s);
 cudaError_t iso_launch_dist(const isod::DistParams& p, cudaStream_t s);
+cudaError_t iso_launch_range(const isod::RangeParams& p, int K, cudaStream_t s);

@@ -82,6 +82,15 @@ int fail(int code, const char* what, cudaError_t e) {
     return code;
 }
 
+// The same, for failures after work was enqueued on `stream`: waits for that
+// work first (ignoring the result), so the next call never reuses the array
+// while this call's kernels or copies still run on it.
+int fail_enqueued(int code, const char* what, cudaError_t e, cudaStream_t stream) {
+    cudaStreamSynchronize(stream);
+    cudaGetLastError();
+    return fail(code, what, e);
+}
+
 }  // namespace
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
@@ -111,6 +120,11 @@ extern "C" int iso_query_noalloc(iso_graph* g, int32_t k, const int32_t* sources
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(ISO_E_CUDA, "cudaGetDevice", e);
     if (dev < 0 || dev >= 64) { iso::set_error("iso_query_noalloc: device id %d unsupported", dev); return ISO_E_INVAL; }
+    if (dev != gv.device) {
+        // the kernels would get another GPU's graph pointers and scratch
+        iso::set_error("iso_query_noalloc: the graph lives on device %d but device %d is current", gv.device, dev);
+        return ISO_E_INVAL;
+    }
     if (!g_base[dev]) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_scratch);
@@ -142,26 +156,26 @@ extern "C" int iso_query_noalloc(iso_graph* g, int32_t k, const int32_t* sources
         }
     }
     if ((e = cudaMemcpyAsync(io, h_io, sizeof h_io, cudaMemcpyHostToDevice, stream)) != cudaSuccess)
-        return fail(ISO_E_CUDA, "input copy", e);
+        return fail_enqueued(ISO_E_CUDA, "input copy", e, stream);
     if (dev_s && k && (e = cudaMemcpyAsync(io, sources, (size_t)k * 4, cudaMemcpyDeviceToDevice, stream)))
-        return fail(ISO_E_CUDA, "input copy", e);
+        return fail_enqueued(ISO_E_CUDA, "input copy", e, stream);
     if (dev_t && k && (e = cudaMemcpyAsync(io + kLanes, taus, (size_t)k * 4, cudaMemcpyDeviceToDevice, stream)))
-        return fail(ISO_E_CUDA, "input copy", e);
+        return fail_enqueued(ISO_E_CUDA, "input copy", e, stream);
     // state that must start at zero: control block (status, barrier, counters) and flags
     if ((e = cudaMemsetAsync(ctl, 0, kCtlWords * 4, stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(base + kOffFlag, 0, (size_t)gv.n, stream)) != cudaSuccess)
-        return fail(ISO_E_CUDA, "clearing scratch", e);
+        return fail_enqueued(ISO_E_CUDA, "clearing scratch", e, stream);
     // one grid-wide step per level
     for (int j = 0; j < gv.L; ++j) g_sched[j] = make_int4(kStepWide, j, j + 1, 0);
     if ((e = cudaMemcpyAsync(base + kOffSched, g_sched, (size_t)gv.L * sizeof(int4), cudaMemcpyHostToDevice,
                              stream)) != cudaSuccess)
-        return fail(ISO_E_CUDA, "schedule copy", e);
+        return fail_enqueued(ISO_E_CUDA, "schedule copy", e, stream);
 
     UpParams up{};
     up.up_off = gv.up_off; up.up_arc = gv.up_arc; up.pos = gv.pos; up.src = io; up.tau = io + kLanes;
     up.pairs = (int2*)(base + kOffPairs); up.cnt = ctl + 8 + kLanes; up.gtab = (uint32_t*)(base + kOffTab);
     up.status = ctl; up.n = gv.n; up.cap = kUpCap; up.gcap = kUpCap; up.tau_max = gv.tau_max;
-    if ((e = iso_launch_upward(up, kLanes, stream)) != cudaSuccess) return fail(ISO_E_CUDA, "upward launch", e);
+    if ((e = iso_launch_upward(up, kLanes, stream)) != cudaSuccess) return fail_enqueued(ISO_E_CUDA, "upward launch", e, stream);
 
     SweepParams sw{};
     sw.down_off = gv.down_off; sw.down_arc = gv.down_arc; sw.level_off = gv.level_off;
@@ -171,9 +185,9 @@ extern "C" int iso_query_noalloc(iso_graph* g, int32_t k, const int32_t* sources
     sw.nsched = gv.L; sw.cap = kUpCap; sw.last_level_block = gv.L - 1; sw.write_all = 0; sw.bar_extra = 0;
     int block = 0;
     const int occ = iso_sweep_occupancy(kLanes, 1, &block);
-    if (occ <= 0) { iso::set_error("iso_query_noalloc: sweep kernel cannot be resident"); return ISO_E_CUDA; }
+    if (occ <= 0) return fail_enqueued(ISO_E_CUDA, "sweep kernel cannot be resident", cudaGetLastError(), stream);
     if ((e = iso_launch_sweep(sw, kLanes, 1, gv.num_sms * occ, stream)) != cudaSuccess)
-        return fail(ISO_E_CUDA, "sweep launch", e);
+        return fail_enqueued(ISO_E_CUDA, "sweep launch", e, stream);
 
     EmitParams em{};
     em.orig_off = gv.orig_off; em.orig_head = gv.orig_head; em.orig_id = gv.orig_id; em.mask = sw.mask;
@@ -181,7 +195,7 @@ extern "C" int iso_query_noalloc(iso_graph* g, int32_t k, const int32_t* sources
     em.status = ctl;
     em.ecnt = ctl + 8; em.ebuf = (int32_t*)(base + kOffEbuf); em.n = gv.n; em.ecap = kMaxArcs;
     if ((e = iso_launch_emit(em, kLanes, gv.num_sms * 8, stream)) != cudaSuccess)
-        return fail(ISO_E_CUDA, "emit launch", e);
+        return fail_enqueued(ISO_E_CUDA, "emit launch", e, stream);
     GatherParams ga{};
     ga.ebuf = em.ebuf; ga.ecnt = em.ecnt; ga.tmp = (int32_t*)(base + kOffTmp); ga.out = (int32_t*)(base + kOffOut);
     ga.out_off = (int64_t*)(base + kOffOutOff); ga.k = kLanes; ga.ecap = kMaxArcs;
@@ -189,12 +203,12 @@ extern "C" int iso_query_noalloc(iso_graph* g, int32_t k, const int32_t* sources
     ga.key_bits = 1;
     while (ga.key_bits < 31 && (int64_t(1) << ga.key_bits) < gv.m) ++ga.key_bits;
     if ((e = iso_launch_sort_gather(ga, kLanes, stream)) != cudaSuccess)
-        return fail(ISO_E_CUDA, "sort launch", e);
+        return fail_enqueued(ISO_E_CUDA, "sort launch", e, stream);
 
     int32_t h_ctl[kCtlWords];
     if ((e = cudaMemcpyAsync(h_ctl, ctl, sizeof h_ctl, cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
         (e = cudaStreamSynchronize(stream)) != cudaSuccess)
-        return fail(ISO_E_CUDA, "kernels", e);
+        return fail_enqueued(ISO_E_CUDA, "kernels", e, stream);
     if (h_ctl[0] == kStTimeout) { iso::set_error("iso_query_noalloc: a grid barrier timed out"); return ISO_E_TIMEOUT; }
     if (h_ctl[0] == kStBadInput) { iso::set_error("iso_query_noalloc: a source or limit failed validation"); return ISO_E_INVAL; }
     if (h_ctl[0] == kStUpOverflow) {
@@ -211,18 +225,18 @@ extern "C" int iso_query_noalloc(iso_graph* g, int32_t k, const int32_t* sources
         off[i + 1] = off[i] + h_ctl[8 + i];
     }
     const int64_t total = off[k];
+    if (total > 0 && total <= cap && !out_arcs) { iso::set_error("iso_query_noalloc: out_arcs is NULL"); return ISO_E_INVAL; }
     if ((e = cudaMemcpyAsync(out_offsets, off, (size_t)(k + 1) * 8, cudaMemcpyDefault, stream)) != cudaSuccess)
-        return fail(ISO_E_CUDA, "offset copy", e);
+        return fail_enqueued(ISO_E_CUDA, "offset copy", e, stream);
     int rc = ISO_OK;
     if (total > cap) {
         iso::set_error("iso_query_noalloc: %lld arcs do not fit capacity %lld", (long long)total, (long long)cap);
         rc = ISO_E_OVERFLOW;
     } else if (total > 0) {
-        if (!out_arcs) { iso::set_error("iso_query_noalloc: out_arcs is NULL"); return ISO_E_INVAL; }
         if ((e = cudaMemcpyAsync(out_arcs, base + kOffOut, (size_t)total * 4, cudaMemcpyDefault, stream)) !=
             cudaSuccess)
-            return fail(ISO_E_CUDA, "result copy", e);
+            return fail_enqueued(ISO_E_CUDA, "result copy", e, stream);
     }
-    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return fail(ISO_E_CUDA, "result copy", e);
+    if ((e = cudaStreamSynchronize(stream)) != cudaSuccess) return fail_enqueued(ISO_E_CUDA, "result copy", e, stream);
     return rc;
 }

@@ -229,7 +229,42 @@ __global__ void k_dist(DistParams p) {
     }
 }
 
+// Vertices in range (Section 3's other output: the set of vertices in range),
+// as one bitset over original vertex ids per query: a warp takes 32
+// consecutive original ids, reads each one's in-range mask through its sweep
+// position, and for every query i writes the 32-bit word whose bit t is bit i
+// of vertex (v0 + t)'s mask (one ballot per query; lane i % 32 stores it).
+template <int K>
+__global__ void k_range(RangeParams p) {
+    using MaskT = typename MaskOf<K>::T;
+    const MaskT* mask = static_cast<const MaskT*>(p.mask);
+    const int lane = threadIdx.x & 31;
+    const int warps = (int)(gridDim.x * blockDim.x) >> 5;
+    for (int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); (int64_t)w * 32 < p.n; w += warps) {
+        const int v = w * 32 + lane;
+        const unsigned long long m = v < p.n ? (unsigned long long)mask[__ldg(p.pos + v)] : 0ull;
+        for (int i = 0; i < p.k; ++i) {
+            const unsigned word = __ballot_sync(0xffffffffu, (m >> i) & 1ull);
+            if (lane == (i & 31)) p.out[(size_t)i * p.words + w] = word;
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t iso_launch_range(const isod::RangeParams& p, int K, cudaStream_t s) {
+    const int grid = 1024;
+    switch (K) {
+        case 1: k_range<1><<<grid, 256, 0, s>>>(p); break;
+        case 4: k_range<4><<<grid, 256, 0, s>>>(p); break;
+        case 8: k_range<8><<<grid, 256, 0, s>>>(p); break;
+        case 16: k_range<16><<<grid, 256, 0, s>>>(p); break;
+        case 32: k_range<32><<<grid, 256, 0, s>>>(p); break;
+        case 64: k_range<64><<<grid, 256, 0, s>>>(p); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t iso_launch_emit(const isod::EmitParams& p, int K, int grid, cudaStream_t s) {
     switch (K) {
@@ -246,12 +281,8 @@ cudaError_t iso_launch_emit(const isod::EmitParams& p, int K, int grid, cudaStre
 
 cudaError_t iso_launch_sort_gather(const isod::GatherParams& p, int K, cudaStream_t s) {
     const int smem = (kSortSmem + 2 * kMaxBuckets + 1) * 4;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_sort_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    if (cudaError_t e = iso_smem_attr_once(k_sort_gather, smem, attr)) return e;
     k_sort_gather<<<K, kSortThreads, smem, s>>>(p);
     return cudaGetLastError();
 }

@@ -430,42 +430,79 @@ __device__ __forceinline__ void finish_level(const SweepParams& p, const Smem& s
     }
 }
 
+// Label rows and in-range masks of the core vertices from k_core's lane-major
+// output (final, clamped labels): thread t of a warp takes vertex v0 + t,
+// reading lane i's label from row i of the lane-major array (coalesced over
+// the warp) and writing its own label row; bit i of the mask is set iff lane
+// i's label is not kInf.
+template <int K>
+__device__ void core_rows(const SweepParams& p, int warp, int lane) {
+    using MaskT = typename MaskOf<K>::T;
+    const int cn = p.core_n;
+    for (int v0 = ((int)blockIdx.x * (kThreads / 32) + warp) * 32; v0 < cn; v0 += (int)gridDim.x * kThreads) {
+        const int v = v0 + lane;
+        if (v >= cn) continue;
+        const uint32_t* src = p.core_out + v;
+        unsigned long long bits = 0;
+        if constexpr (K >= 4) {
+#pragma unroll 4
+            for (int i = 0; i < K; i += 4) {
+                uint4 x;
+                x.x = __ldcg(src + (size_t)i * cn);
+                x.y = __ldcg(src + (size_t)(i + 1) * cn);
+                x.z = __ldcg(src + (size_t)(i + 2) * cn);
+                x.w = __ldcg(src + (size_t)(i + 3) * cn);
+                bits |= (unsigned long long)(x.x != kInf) << i | (unsigned long long)(x.y != kInf) << (i + 1) |
+                        (unsigned long long)(x.z != kInf) << (i + 2) | (unsigned long long)(x.w != kInf) << (i + 3);
+                reinterpret_cast<uint4*>(p.d + (size_t)v * K)[i / 4] = x;
+            }
+        } else {
+            for (int i = 0; i < K; ++i) {
+                const uint32_t x = __ldcg(src + (size_t)i * cn);
+                bits |= (unsigned long long)(x != kInf) << i;
+                p.d[(size_t)v * K + i] = x;
+            }
+        }
+        static_cast<MaskT*>(p.mask)[v] = (MaskT)bits;
+    }
+}
+
 // Grid-wide barrier of the whole CTA (the launch is cooperative, so every CTA
-// is resident).  Bounded: gives up, recording kStTimeout, after the timeout
-// (bar_extra adds arrivals that never come, for the tests).  Returns false,
-// the same on every thread of the CTA, if the kernel has failed.
-__device__ bool grid_sync(const SweepParams& p) {
+// is resident).  The arrival counter p.bar[0] (zeroed per batch) only grows:
+// barrier number e of the launch is passed once it reaches e * gridDim.x, so
+// an arrival is one release-add and a wait is acquire-polling of the counter,
+// with no reset between barriers.  Bounded: gives up, recording kStTimeout,
+// after the timeout (bar_extra adds arrivals that never come, for the tests).
+// Returns false, the same on every thread of the CTA, if the kernel has failed.
+__device__ __forceinline__ void red_release_add(uint32_t* a, uint32_t v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* a) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+    return v;
+}
+
+__device__ bool grid_sync(const SweepParams& p, uint32_t& epoch) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        volatile int32_t* st = p.status;
-        volatile uint32_t* gen = p.bar + 1;
-        if (*st != kStOk) {
-            ok = 0;
-        } else {
-            const uint32_t g0 = *gen;
-            fence_acq_rel_gpu();
-            const uint32_t want = gridDim.x + (uint32_t)p.bar_extra;
-            if (atomicAdd(p.bar, 1u) + 1u == want) {
-                atomicExch(p.bar, 0u);
-                fence_acq_rel_gpu();
-                atomicAdd(p.bar + 1, 1u);
-            } else {
-                const unsigned long long t0 = global_ns();
-                for (uint32_t it = 0; *gen == g0; ++it) {
-                    if ((it & 15) == 15) {
-                        if (*st != kStOk) { ok = 0; break; }
-                        if (global_ns() - t0 > (unsigned long long)p.timeout_ns || it > (1u << 28)) {
-                            atomicCAS(p.status, kStOk, kStTimeout);
-                            ok = 0;
-                            break;
-                        }
-                    }
+        ++epoch;
+        const uint32_t want = epoch * gridDim.x + (uint32_t)p.bar_extra;
+        red_release_add(p.bar, 1u);  // this CTA's writes (ordered by the CTA barrier) before the arrival
+        const unsigned long long t0 = global_ns();
+        for (uint32_t it = 0; ld_acquire(p.bar) < want; ++it) {
+            if ((it & 15) == 15) {
+                if (*(volatile int32_t*)p.status != kStOk) { ok = 0; break; }
+                if (global_ns() - t0 > (unsigned long long)p.timeout_ns || it > (1u << 28)) {
+                    atomicCAS(p.status, kStOk, kStTimeout);
+                    ok = 0;
+                    break;
                 }
             }
-            fence_acq_rel_gpu();
         }
+        if (ok && *(volatile int32_t*)p.status != kStOk) ok = 0;
         s_ok = ok;
     }
     __syncthreads();
@@ -545,7 +582,18 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_sweep_tma(SweepPa
     // chunks of this CTA: positions blockIdx.x, blockIdx.x + G, ...
     const int G = (int)gridDim.x;
     const int n_mine = (int)blockIdx.x < p.Q ? (p.Q - (int)blockIdx.x + G - 1) / G : 0;
+    uint32_t epoch = 0;  // grid barriers passed (thread 0's count)
 
+    // (with a per-lane core, k_core has recorded the start of the sweep step)
+    if (p.trace && tid == 0 && blockIdx.x == 0 && p.core_levels == 0)
+        p.trace[0] = p.trace[p.L + 1] = (long long)global_ns();
+    // The per-lane core (k_core, launched just before) has left the final
+    // labels of its vertices lane-major; they become label rows and masks here,
+    // complete for every CTA after a grid barrier.
+    if (p.core_levels > 0) {
+        core_rows<K>(p, warp, lane);
+        if (!grid_sync(p, epoch)) return;  // the same in every thread of the CTA
+    }
     if (tid == 0) {
         for (int i = 0; i < kStages; ++i) {
             mbar_init(&sm.full[i], 1);
@@ -559,7 +607,6 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_sweep_tma(SweepPa
         const int32_t t = p.tau[tid];
         sm.tau[tid] = t < 0 ? 0u : (uint32_t)t;
     }
-    if (p.trace && tid == 0 && blockIdx.x == 0) p.trace[0] = p.trace[p.L + 1] = (long long)global_ns();
     __syncthreads();
 
     // ---------------- the leading levels, level by level ----------------
@@ -567,21 +614,21 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_sweep_tma(SweepPa
     // the smallest alone (a CTA barrier per level), then all CTAs sweep the
     // other narrow ones (a grid barrier per level).  The schedule holds no
     // chunks of these levels and no dependencies on them.
-    if (p.sync_levels > 0) {
+    if (p.sync_levels > p.core_levels) {
         bool ok = true;
         // plans read graph data only, so each is made before the barrier that
         // ends the level in front of it
         const bool grid_levels = p.solo_levels < p.sync_levels;
         LevelPlan pl{};
         if (grid_levels) pl = plan_level<TPV>(p, p.solo_levels, warp, tid);
-        if (p.solo_levels > 0) {
-            if (blockIdx.x == 0) sweep_levels_cta<K, TPV>(p, sm, 0, p.solo_levels, warp, tid);
-            ok = grid_sync(p);
+        if (p.solo_levels > p.core_levels) {
+            if (blockIdx.x == 0) sweep_levels_cta<K, TPV>(p, sm, p.core_levels, p.solo_levels, warp, tid);
+            ok = grid_sync(p, epoch);
         }
         for (int j = p.solo_levels; ok && j < p.sync_levels; ++j) {
             finish_level<K, TPV>(p, sm, j, pl, tid);
             if (j + 1 < p.sync_levels) pl = plan_level<TPV>(p, j + 1, warp, tid);
-            ok = grid_sync(p);
+            ok = grid_sync(p, epoch);
             if (ok && p.trace && tid == 0 && blockIdx.x == 0)
                 atomicMax((unsigned long long*)p.trace + 1 + j, global_ns());
         }
@@ -599,6 +646,9 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_sweep_tma(SweepPa
         int cur = -1;             // chunk in my stage not posted yet, or -1
         int cur_pa = 0, cur_np = 0;
         bool cur_held = false;    // its dependency list was copied to shared memory
+        // staging limits (the buffer sizes, or lower ones a test asks for)
+        const int arc_cap = p.stage_arc_cap > 0 && p.stage_arc_cap < kArcCap ? p.stage_arc_cap : kArcCap;
+        const int pred_cap = p.stage_pred_cap > 0 && p.stage_pred_cap < kPredCap ? p.stage_pred_cap : kPredCap;
         int posted = 0;
         // schedule record of chunk t, loaded one chunk ahead so that issuing
         // never waits for it
@@ -619,9 +669,9 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_sweep_tma(SweepPa
                 const int4 c1 = n1;  // arc base, arcs, deps start, deps
                 const int ob = c0.x & ~3;
                 const uint32_t obytes = (uint32_t)(((c0.y + 1 - ob) * 4 + 15) & ~15);
-                const int big = c1.y > kArcCap;
+                const int big = c1.y > arc_cap;
                 const uint32_t abytes = big ? 0u : (uint32_t)((c1.y * 8 + 15) & ~15);
-                cur_held = c1.w <= kPredCap && p.bar_extra == 0;
+                cur_held = c1.w <= pred_cap && p.bar_extra == 0;
                 const uint32_t pbytes = cur_held ? (uint32_t)(((c1.w + 3) & ~3) * 4) : 0u;
                 sm.meta[lane] = Meta{c0.x, c0.y, c1.x, big | (c0.w ? 2 : 0), pos, c0.z, {0, 0}};
                 mbar_expect_tx(&sm.full[lane], obytes + abytes + pbytes);
@@ -735,19 +785,19 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_sweep_tma(SweepPa
     __syncthreads();
 }
 
+// Dynamic shared memory of a CTA.  Kept to the chunk phase's buffers: the
+// shared memory a CTA takes comes out of the SM's L1, which also holds the
+// gathers in flight (a larger carve-out measurably slowed the chunk phase).
+constexpr size_t kSmemBytes = sizeof(Smem);
+
 template <int K, int TPV>
 cudaError_t launch(const SweepParams& p, int grid, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_sweep_tma<K, TPV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sizeof(Smem));
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    if (cudaError_t e = iso_smem_attr_once(k_sweep_tma<K, TPV>, (int)kSmemBytes, attr)) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = sizeof(Smem);
+    cfg.dynamicSmemBytes = kSmemBytes;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeCooperative;
@@ -759,15 +809,10 @@ cudaError_t launch(const SweepParams& p, int grid, cudaStream_t s) {
 
 template <int K, int TPV>
 int occupancy() {
-    static bool attr = false;
-    if (!attr) {
-        if (cudaFuncSetAttribute(k_sweep_tma<K, TPV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(Smem)) != cudaSuccess)
-            return 0;
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    if (iso_smem_attr_once(k_sweep_tma<K, TPV>, (int)kSmemBytes, attr) != cudaSuccess) return 0;
     int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_sweep_tma<K, TPV>, kThreads, sizeof(Smem)) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_sweep_tma<K, TPV>, kThreads, kSmemBytes) !=
         cudaSuccess)
         return 0;
     return blocks;
@@ -776,6 +821,11 @@ int occupancy() {
 #define ISO_TMA_CASES(X) X(1, 1) X(4, 1) X(8, 1) X(16, 2) X(16, 4) X(32, 4) X(32, 8) X(64, 8) X(64, 16)
 
 }  // namespace
+
+void iso_sweep_tma_stage_caps(int* arcs, int* deps) {
+    *arcs = kArcCap;
+    *deps = kPredCap;
+}
 
 bool iso_sweep_tma_supported(int K, int tpv) {
 #define X(k, t) if (K == k && tpv == t) return true;

@@ -59,7 +59,7 @@ __device__ __forceinline__ Table carve(uint32_t* base, uint32_t slots) {
 
 // Runs the search with table t.  Returns false if the table overflowed.
 __device__ bool search(const Table& t, const UpParams& p, int32_t s, uint32_t tau, int lane) {
-    __shared__ int s_used, s_nfr, s_next, s_over, s_out;
+    __shared__ int s_used, s_nfr, s_next, s_over, s_out, s_core;
     const uint32_t slots = t.mask + 1;
     const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     for (uint32_t i = threadIdx.x; i < slots; i += blockDim.x) {
@@ -67,7 +67,7 @@ __device__ bool search(const Table& t, const UpParams& p, int32_t s, uint32_t ta
         t.dist[i] = kInf;
     }
     for (uint32_t i = threadIdx.x; i < slots / 32; i += blockDim.x) t.queued[i] = 0;
-    if (threadIdx.x == 0) { s_used = 0; s_over = 0; s_out = 0; }
+    if (threadIdx.x == 0) { s_used = 0; s_over = 0; s_out = 0; s_core = 0; }
     __syncthreads();
     if (threadIdx.x == 0) {
         const int sl = find_or_insert(t, s, &s_used);
@@ -107,16 +107,24 @@ __device__ bool search(const Table& t, const UpParams& p, int32_t s, uint32_t ta
     }
     if (s_over) return false;
     if (p.direct) {
-        // labels go straight into their row slots; other lanes own the other slots
+        // labels go straight into their row slots (other lanes own the other
+        // slots); those of the top core [0, core_n), which the sweep resolves
+        // per lane, go to the lane's pair list instead
+        int2* core = p.pairs + (size_t)lane * p.cap;
         for (uint32_t i = threadIdx.x; i < slots; i += blockDim.x) {
             const int32_t v = t.key[i];
             if (v >= 0) {
-                p.d[(size_t)v * p.K + lane] = t.dist[i];
-                atomicOr(p.upmask + v, 1ull << lane);
-                p.upflag[v] = 1;
-                atomicAdd(&s_out, 1);
+                if (v < p.core_n) {
+                    core[atomicAdd(&s_core, 1)] = make_int2(v, (int)t.dist[i]);
+                } else {
+                    p.d[(size_t)v * p.K + lane] = t.dist[i];
+                    atomicOr(p.upmask + v, 1ull << lane);
+                    p.upflag[v] = 1;
+                }
             }
         }
+        __syncthreads();
+        if (threadIdx.x == 0) s_out = s_core;
     } else {
         int2* out = p.pairs + (size_t)lane * p.cap;
         for (uint32_t i = threadIdx.x; i < slots; i += blockDim.x) {
@@ -159,12 +167,8 @@ size_t iso_upward_table_words(size_t gcap) { return table_words(gcap); }
 
 cudaError_t iso_launch_upward(const isod::UpParams& p, int K, cudaStream_t s) {
     const size_t smem = table_words(kSmemSlots) * 4;  // 194 KB
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_upward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    if (cudaError_t e = iso_smem_attr_once(k_upward, (int)smem, attr)) return e;
     k_upward<<<K, kThreads, smem, s>>>(p);
     return cudaGetLastError();
 }

@@ -1,15 +1,25 @@
 """Continuous-batching isochrone server.
 
 Requests (source, tau) arrive at any time and wait in one queue.  The server
-keeps the graph resident and holds several workspaces (per-batch device
-buffers, each with its own CUDA stream); how many is decided by device memory.
-Each workspace has a worker thread that repeatedly takes whatever requests are
-waiting -- up to its number of lanes -- submits them as one batch, collects the
-results and completes the requests' futures.  A request therefore joins the
-next batch that starts after it arrives, on whichever workspace frees up
-first, while other batches are still on the device.  The library calls release
-the GIL, so the workers overlap host work (input copies, result copies) with
-device work of the other batches.
+keeps the graph resident and holds a pool of workspaces (per-batch device
+buffers, each with its own CUDA stream).  Each workspace has a worker thread
+that repeatedly takes whatever requests are waiting -- up to its number of
+lanes -- submits them as one batch, collects the results and completes the
+requests.  A request therefore joins the next batch that starts after it
+arrives, on whichever workspace frees up first, while other batches are still
+on the device.  The library calls release the GIL, so the workers overlap host
+work (input copies, result copies) with device work of the other batches.
+
+Admission by device memory: the pool starts with `workspaces` workspaces and
+grows by one (up to max_workspaces) whenever requests are left waiting behind
+busy workspaces and the device still has room for another one -- free memory,
+read when the growth is considered, must cover a workspace's measured size
+within `memory_fraction` of what is free.  A workspace is warmed (one batch,
+which also captures its CUDA graph) before it takes requests.
+
+Host work per batch is kept out of per-request Python: requests are taken from
+the queue in one locked step, the batch's results are split into views of one
+array, and one event per batch completes all of its requests.
 
 Each request's result is exactly what a query of that request alone returns:
 lanes of a batch never interact (every lane has its own labels, limit and
@@ -18,11 +28,10 @@ output list).
 
 from __future__ import annotations
 
+import collections
 import dataclasses
-import queue
 import threading
 import time
-from concurrent.futures import Future
 
 import numpy as np
 
@@ -41,78 +50,136 @@ class Result:
         return (self.t_done - self.t_arrival) * 1e3
 
 
+class _Batch:
+    """The answer of one batch, shared by its requests: one event completes all."""
+    __slots__ = ("event", "off", "arcs", "error", "t_done", "bid")
+
+    def __init__(self):
+        self.event = threading.Event()
+        self.off = self.arcs = self.error = None
+        self.t_done = 0.0
+        self.bid = -1
+
+
+class Pending:
+    """Handle of a queued request (a minimal future: result(timeout), done())."""
+    __slots__ = ("source", "tau", "t_arrival", "batch", "index")
+
+    def __init__(self, source: int, tau: int, t_arrival: float):
+        self.source, self.tau, self.t_arrival = source, tau, t_arrival
+        self.batch: _Batch | None = None
+        self.index = -1
+
+    def done(self) -> bool:
+        b = self.batch
+        return b is not None and b.event.is_set()
+
+    def result(self, timeout: float | None = None) -> Result:
+        deadline = None if timeout is None else time.perf_counter() + timeout
+        while self.batch is None:  # not yet taken into a batch
+            if deadline is not None and time.perf_counter() > deadline:
+                raise TimeoutError("request not answered in time")
+            time.sleep(50e-6)
+        b = self.batch
+        left = None if deadline is None else max(0.0, deadline - time.perf_counter())
+        if not b.event.wait(left):
+            raise TimeoutError("request not answered in time")
+        if b.error is not None:
+            raise b.error
+        i = self.index
+        return Result(arcs=b.arcs[b.off[i]:b.off[i + 1]], t_arrival=self.t_arrival, t_done=b.t_done, batch=b.bid)
+
+
 class IsoServer:
     """Serve isochrone queries on one device graph with continuous batching.
 
-    lanes: queries per batch (1..64).  workspaces: number of batches in flight;
-    None = as many as fit in `memory_fraction` of the free device memory (at
-    most max_workspaces).  warm: run one small batch on every workspace before
-    taking requests, so that no request waits for a workspace's first launch
-    (CUDA-graph capture, sweep schedule upload).  Extra keyword options go to
-    the workspaces (iso_query_opts fields)."""
+    lanes: queries per batch (1..64).  workspaces: batches in flight at start
+    (None = 1).  max_workspaces: the most the pool grows to while device memory
+    allows (see the module docstring).  warm: run one batch on every workspace
+    before it takes requests, so that no request waits for a workspace's first
+    launch (CUDA-graph capture, sweep schedule upload).  Extra keyword options
+    go to the workspaces (iso_query_opts fields)."""
 
     def __init__(self, g: _lib.DeviceGraph, lanes: int = 64, workspaces: int | None = None,
                  memory_fraction: float = 0.5, max_workspaces: int = 4, warm: bool = True, **opts):
         import torch
+        self.torch = torch
         self.g = g
         self.lanes = lanes
+        self.opts = dict(opts)
+        self.opts.setdefault("use_cuda_graph", 1)
+        self.memory_fraction = memory_fraction
+        self.max_workspaces = max(1, max_workspaces)
+        self.warm = warm
         self._init_state()
-        opts.setdefault("use_cuda_graph", 1)
         free0, _ = torch.cuda.mem_get_info()
-        first = _lib.Workspace(g, lanes, **opts)
+        first = self._new_workspace()
         torch.cuda.synchronize()
         free1, _ = torch.cuda.mem_get_info()
-        per_ws = max(free0 - free1, 1)
-        if workspaces is None:
-            fit = int(free1 * memory_fraction // per_ws)
-            workspaces = max(1, min(max_workspaces, 1 + fit))
-        self.workspaces = [first] + [_lib.Workspace(g, lanes, **opts) for _ in range(workspaces - 1)]
-        self.bytes_per_workspace = per_ws
-        if warm:
-            src = np.zeros(lanes, np.int32)
-            tau = np.zeros(lanes, np.int32)
-            for ws in self.workspaces:
-                ws.submit(src, tau)
-                ws.collect()
+        self.bytes_per_workspace = max(free0 - free1, 1)
+        self.workspaces = [first]
+        for _ in range(max(1, workspaces or 1) - 1):
+            self.workspaces.append(self._new_workspace())
+        self.grown = 0          # workspaces added while serving
+        self.refused_growth = 0  # growths refused for lack of device memory
         self._start_workers()
 
     @classmethod
     def over_workspaces(cls, workspaces, lanes: int) -> "IsoServer":
         """A server over ready-made workspaces: objects with submit(sources, taus)
         and collect() -> (offsets, arcs, dist), as _lib.Workspace has.  No device
-        set-up happens here."""
+        set-up happens here and the pool does not grow."""
         self = cls.__new__(cls)
         self.g = None
         self.lanes = lanes
+        self.max_workspaces = len(workspaces)
         self._init_state()
         self.workspaces = list(workspaces)
         self.bytes_per_workspace = 0
+        self.grown = self.refused_growth = 0
         self._start_workers()
         return self
 
     def _init_state(self):
-        self._q: queue.Queue = queue.Queue()
-        self._stop = threading.Event()
+        self._q: collections.deque = collections.deque()
+        self._cv = threading.Condition()
+        self._stop = False
         self._batch_id = 0
-        self._id_lock = threading.Lock()
+        self._busy = 0
+        self._growing = False
+        self._threads: list[threading.Thread] = []
+
+    def _new_workspace(self):
+        ws = _lib.Workspace(self.g, self.lanes, **self.opts)
+        if self.warm:
+            z = np.zeros(self.lanes, np.int32)
+            ws.submit(z, z)
+            ws.collect()
+        return ws
 
     def _start_workers(self):
-        self._threads = [threading.Thread(target=self._worker, args=(ws,), daemon=True) for ws in self.workspaces]
-        for t in self._threads:
-            t.start()
+        for ws in self.workspaces:
+            self._spawn(ws)
+
+    def _spawn(self, ws):
+        t = threading.Thread(target=self._worker, args=(ws,), daemon=True)
+        self._threads.append(t)
+        t.start()
 
     # ------------------------------------------------------------------ client side
-    def submit(self, source: int, tau: int) -> Future:
-        """Queue one query; the future's result is a Result."""
-        f: Future = Future()
-        self._q.put((int(source), int(tau), time.perf_counter(), f))
-        return f
+    def submit(self, source: int, tau: int) -> Pending:
+        """Queue one query; the handle's result() is a Result."""
+        p = Pending(int(source), int(tau), time.perf_counter())
+        with self._cv:
+            self._q.append(p)
+            self._cv.notify()
+        return p
 
     def close(self):
-        self._stop.set()
-        for _ in self._threads:
-            self._q.put(None)
-        for t in self._threads:
+        with self._cv:
+            self._stop = True
+            self._cv.notify_all()
+        for t in list(self._threads):
             t.join()
 
     def __enter__(self):
@@ -121,43 +188,73 @@ class IsoServer:
     def __exit__(self, *a):
         self.close()
 
+    # ------------------------------------------------------------------ admission
+    def _maybe_grow(self):
+        """Called with the lock held when requests wait behind busy workspaces:
+        add a workspace in the background if the pool may grow and device
+        memory has room for it."""
+        if self.g is None or self._growing or len(self.workspaces) >= self.max_workspaces:
+            return
+        self._growing = True
+        threading.Thread(target=self._grow, daemon=True).start()
+
+    def _grow(self):
+        try:
+            free, _ = self.torch.cuda.mem_get_info()
+            if free * self.memory_fraction < self.bytes_per_workspace:
+                self.refused_growth += 1
+                return
+            ws = self._new_workspace()
+            with self._cv:
+                if self._stop:
+                    ws.free()
+                    return
+                self.workspaces.append(ws)
+                self.grown += 1
+                self._spawn(ws)
+        except Exception:  # out of memory or a failed launch: keep the pool as it is
+            self.refused_growth += 1
+        finally:
+            with self._cv:
+                self._growing = False
+
     # ------------------------------------------------------------------ workers
     def _take_batch(self):
-        first = self._q.get()
-        if first is None:
-            return None
-        batch = [first]
-        while len(batch) < self.lanes:
-            try:
-                item = self._q.get_nowait()
-            except queue.Empty:
-                break
-            if item is None:          # shutting down: let another worker see it
-                self._q.put(None)
-                break
-            batch.append(item)
-        return batch
+        with self._cv:
+            while not self._q and not self._stop:
+                self._cv.wait()
+            if not self._q:
+                return None
+            n = min(self.lanes, len(self._q))
+            batch = [self._q.popleft() for _ in range(n)]
+            self._busy += 1
+            if self._q and self._busy >= len(self.workspaces):
+                self._maybe_grow()
+            b = _Batch()
+            b.bid = self._batch_id
+            self._batch_id += 1
+        for i, p in enumerate(batch):
+            p.index = i
+            p.batch = b
+        return batch, b
 
-    def _worker(self, ws: _lib.Workspace):
-        while not self._stop.is_set():
-            batch = self._take_batch()
-            if batch is None:
+    def _worker(self, ws):
+        while True:
+            got = self._take_batch()
+            if got is None:
                 return
-            with self._id_lock:
-                bid = self._batch_id
-                self._batch_id += 1
-            srcs = np.array([b[0] for b in batch], np.int32)
-            taus = np.array([b[1] for b in batch], np.int32)
+            batch, b = got
+            srcs = np.fromiter((p.source for p in batch), np.int32, len(batch))
+            taus = np.fromiter((p.tau for p in batch), np.int32, len(batch))
             try:
                 ws.submit(srcs, taus)
-                off, arcs, _ = ws.collect()
-            except Exception as e:  # report to every request of the batch
-                for b in batch:
-                    b[3].set_exception(e)
-                continue
-            t = time.perf_counter()
-            for i, b in enumerate(batch):
-                b[3].set_result(Result(arcs=arcs[off[i]:off[i + 1]].copy(), t_arrival=b[2], t_done=t, batch=bid))
+                b.off, b.arcs, _ = ws.collect()
+            except Exception as e:  # reported to every request of the batch
+                b.error = e
+            b.t_done = time.perf_counter()
+            b.event.set()
+            with self._cv:
+                self._busy -= 1
 
 
 def run_poisson(server: IsoServer, sources: np.ndarray, taus: np.ndarray, arrivals_s: np.ndarray):

@@ -41,10 +41,33 @@ def test_sweep_bytes_definition():
     assert bench.sweep_bytes(A, 64, write_all=True)["d_write"] == 4 * k * n
 
 
-def test_traffic_only_for_the_captured_sources():
+def test_sweep_bytes_scope_definition():
+    """The roofline's numerator: 4(n+1) + 8 m_down + 4kn + 4kn + 4(L+1)."""
     sys.path.insert(0, ROOT)
     import bench
-    assert bench.sweep_traffic("no-such-workload") is None
-    h, t = bench.SWEEP_TRAFFIC["grid18m_k64"]
-    got = bench.sweep_traffic("grid18m_k64")
-    assert got == (t if h == bench.sweep_source_hash() else None)
+    A = {"perm": np.arange(6), "level_off": np.array([0, 1, 3, 6]), "down_src": np.array([0, 0, 1, 2])}
+    n, k, L, m_down = 6, 64, 3, 4
+    assert sum(bench.sweep_bytes_scope(A, k).values()) == 4 * (n + 1) + 8 * m_down + 8 * k * n + 4 * (L + 1)
+    # 18M grid at 64 lanes: 9.990 GB
+    n, m_down, L = 18_003_049, 87_496_783, 191
+    big = {"perm": np.zeros(n, np.int8), "down_src": np.zeros(m_down, np.int8), "level_off": np.zeros(L + 1)}
+    assert round(sum(bench.sweep_bytes_scope(big, 64).values()) / 1e9, 3) == 9.990
+    assert [bench.lanes_class(k) for k in (1, 2, 5, 16, 17, 64)] == [1, 4, 8, 16, 32, 64]
+
+
+def test_traffic_only_for_the_captured_sources_and_options():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.sweep_traffic("no-such-workload", {}) is None
+    saved = dict(bench.SWEEP_TRAFFIC)
+    try:
+        h = bench.sweep_source_hash()
+        bench.SWEEP_TRAFFIC["w"] = (h, {"schedule_delay": 608}, 123)
+        assert bench.sweep_traffic("w", {"schedule_delay": 608, "use_cuda_graph": 1}) == 123
+        assert bench.sweep_traffic("w", {"schedule_delay": 304}) is None     # other options
+        assert bench.sweep_traffic("w", {"schedule_delay": 608, "chunk_span": 2500}) is None
+        bench.SWEEP_TRAFFIC["w"] = ("0" * 16, {"schedule_delay": 608}, 123)
+        assert bench.sweep_traffic("w", {"schedule_delay": 608}) is None     # other sources
+    finally:
+        bench.SWEEP_TRAFFIC.clear()
+        bench.SWEEP_TRAFFIC.update(saved)

@@ -132,7 +132,7 @@ def test_top_block_sizes(solo, graph):
     g, dg = dev_graph("grid64")
     srcs = synth.draw_sources(g, 16, 15)
     taus = synth.draw_taus_uniform(16, 0, 3000, 16)
-    check_batch(g, dg, srcs, taus, solo_width=solo, use_cuda_graph=graph, sweep_kernel=1)
+    check_batch(g, dg, srcs, taus, solo_width=solo, use_cuda_graph=graph, sweep_kernel=1, core_vertices=-1)
 
 
 @pytest.mark.parametrize("solo,fuse", [(-1, -1), (124, -1), (-1, 0), (1 << 30, 0), (124, 1 << 20), (-1, 1 << 20)])
@@ -144,7 +144,8 @@ def test_leading_level_phases(solo, fuse):
     g, dg = dev_graph("grid1k")
     srcs = synth.draw_sources(g, 16, 61)
     taus = synth.draw_taus_uniform(16, 0, 60000, 62)
-    check_batch(g, dg, srcs, taus, want_dist=True, solo_width=solo, fuse_width=fuse, sweep_kernel=1)
+    check_batch(g, dg, srcs, taus, want_dist=True, solo_width=solo, fuse_width=fuse, sweep_kernel=1,
+                core_vertices=-1)
 
 
 @pytest.mark.parametrize("span", [512, 4096])
@@ -162,7 +163,74 @@ def test_top_block_grid1k(solo):
     g, dg = dev_graph("grid1k")
     srcs = synth.draw_sources(g, 64, 51)
     taus = synth.draw_taus_uniform(64, 0, 60000, 52)
-    check_batch(g, dg, srcs, taus, want_dist=True, solo_width=solo, sweep_kernel=1)
+    check_batch(g, dg, srcs, taus, want_dist=True, solo_width=solo, sweep_kernel=1, core_vertices=-1)
+
+
+@pytest.mark.parametrize("core", [-1, 1, 200, 5000, 0])
+@pytest.mark.parametrize("k", [1, 5, 16, 64])
+def test_per_lane_core_grid1k(core, k):
+    # core 1 / 200 / 5000: the top level blocks within that many vertices are
+    # swept per lane in shared memory (1: just the top level), then grid
+    # barriers, then chunks; 0: as many as fit; -1: none
+    g, dg = dev_graph("grid1k")
+    srcs = synth.draw_sources(g, k, 81 + k)
+    taus = synth.draw_taus_uniform(k, 0, 60000, 82 + k)
+    check_batch(g, dg, srcs, taus, want_dist=True, core_vertices=core, sweep_kernel=1)
+
+
+@pytest.mark.parametrize("arcs,deps", [(64, 0), (0, 1), (16, 1), (1, 1)])
+def test_global_memory_staging_paths(arcs, deps):
+    # lower staging limits force the sweep's two global-memory paths: chunks
+    # whose arc block exceeds the stage buffer read their arcs from global
+    # memory, and dependency lists longer than the held list are checked there
+    g, dg = dev_graph("grid1k")
+    opts = dict(debug_stage_arcs=arcs, debug_stage_deps=deps, sweep_kernel=1)
+    ws = P.Workspace(dg, 16, **opts)
+    info = ws.sweep_info()
+    ws.free()
+    assert info["arc_cap"] == (arcs or 3072) and info["dep_cap"] == (deps or 128)
+    if arcs:
+        assert info["chunks_over_arc_cap"] > 0
+    if deps:
+        assert info["chunks_over_dep_cap"] > 0
+    srcs = synth.draw_sources(g, 16, 97)
+    taus = synth.draw_taus_uniform(16, 0, 60000, 98)
+    check_batch(g, dg, srcs, taus, want_dist=True, **opts)
+
+
+def test_sweep_info_describes_the_phases():
+    g, dg = dev_graph("grid1k")
+    ws = P.Workspace(dg, 64)
+    info = ws.sweep_info()
+    ws.free()
+    assert info["levels"] == dg.levels
+    assert 0 < info["core_levels"] <= info["solo_levels"] <= info["sync_levels"] <= info["levels"]
+    assert 0 < info["core_vertices"] <= 53248 and info["chunks"] > 0
+    assert info["max_chunk_arcs"] > 0 and info["max_chunk_deps"] > 0
+
+
+@pytest.mark.parametrize("graph", [0, 1])
+def test_per_lane_core_sources_inside_the_core(graph):
+    # sources at the top of the hierarchy (their upward labels are all core
+    # labels) mixed with ordinary ones, fused and unfused narrow levels
+    g, ch = workload("grid1k")
+    _, dg = dev_graph("grid1k")
+    perm = ch.arrays()["perm"]
+    srcs = np.concatenate([perm[[0, 1, 7, 100, 3000, 40000]], synth.draw_sources(g, 10, 91)]).astype(np.int32)
+    taus = synth.draw_taus_uniform(len(srcs), 0, 60000, 92)
+    for fuse in (0, -1):
+        check_batch(g, dg, srcs, taus, want_dist=True, sweep_kernel=1, fuse_width=fuse, use_cuda_graph=graph)
+
+
+@pytest.mark.parametrize("k", [1, 3, 64])
+def test_per_lane_core_covers_the_whole_graph(k):
+    # grid64 (4,096 vertices) fits the core: every level is swept per lane and
+    # the chunk schedule is empty
+    g, dg = dev_graph("grid64")
+    srcs = synth.draw_sources(g, k, 95)
+    taus = synth.draw_taus_uniform(k, 0, 3000, 96)
+    check_batch(g, dg, srcs, taus, want_dist=True, sweep_kernel=1)
+    check_batch(g, dg, srcs, taus, want_dist=False, sweep_kernel=1, use_cuda_graph=1)
 
 
 def test_duplicate_sources_and_extreme_limits():
@@ -264,13 +332,46 @@ def test_argument_errors_and_recovery():
     check_batch(g, dg, synth.draw_sources(g, 4, 9), np.full(4, 900, np.int32))
 
 
-@pytest.mark.parametrize("kernel", [1, 2])
-def test_barrier_timeout_is_reported_and_context_survives(kernel):
-    g, dg = dev_graph("grid64")
+@pytest.mark.parametrize("kernel,core,graph", [(1, 0, "grid64"), (1, -1, "grid64"), (1, 0, "grid1k"),
+                                                (1, -1, "grid1k"), (2, 0, "grid64")])
+def test_barrier_timeout_is_reported_and_context_survives(kernel, core, graph):
+    # every device-side wait of the sweep gives up after the timeout: the grid
+    # barrier after the per-lane core (core 0; on grid64 the core is the whole
+    # graph), the leading levels' barriers and the chunks' dependency waits
+    g, dg = dev_graph(graph)
     srcs = synth.draw_sources(g, 4, 2)
     taus = np.full(4, 1000, np.int32)
     with pytest.raises(P.IsoError) as e:
-        P.iso_query(dg, srcs, taus, debug_barrier_extra=1, barrier_timeout_ns=20_000_000, sweep_kernel=kernel)
+        P.iso_query(dg, srcs, taus, debug_barrier_extra=1, barrier_timeout_ns=20_000_000, sweep_kernel=kernel,
+                    core_vertices=core)
     assert e.value.code == P.ISO_E_TIMEOUT
     torch.cuda.synchronize()
-    check_batch(g, dg, srcs, taus)
+    check_batch(g, dg, srcs, taus, core_vertices=core, sweep_kernel=kernel)
+
+
+def _unpack(bits, n):
+    return np.unpackbits(np.ascontiguousarray(bits).view(np.uint8), axis=1, bitorder="little")[:, :n].astype(bool)
+
+
+@pytest.mark.parametrize("k", [1, 13, 64])
+def test_vertices_in_range_bitsets(k):
+    # the other output Section 3 names: per query, the set of vertices in range
+    g, dg = dev_graph("grid1k")
+    srcs = synth.draw_sources(g, k, 101 + k)
+    taus = synth.draw_taus_uniform(k, 0, 60000, 102 + k)
+    ws = P.Workspace(dg, k)
+    with pytest.raises(P.IsoError):
+        ws.collect_range()                       # nothing collected yet
+    ws.submit(srcs, taus)
+    ws.collect()
+    bits = ws.collect_range()
+    _, _, o_dist = oracle.query_batch(g.n, g.tail, g.head, g.weight, srcs, taus, want_dist=True, threads=8)
+    assert np.array_equal(_unpack(bits, g.n), o_dist != INF)
+    # into a device buffer with a longer row pitch (the extra words stay untouched)
+    words = (g.n + 31) // 32
+    dbuf = torch.full((k, words + 5), -1, dtype=torch.int32, device="cuda")
+    ws.collect_range(dbuf)
+    got = dbuf.cpu().numpy()
+    assert np.all(got[:, words:] == -1)
+    assert np.array_equal(got[:, :words].view(np.uint32), bits)
+    ws.free()
