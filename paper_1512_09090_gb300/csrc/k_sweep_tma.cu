@@ -468,41 +468,46 @@ __device__ void core_rows(const SweepParams& p, int warp, int lane) {
 }
 
 // Grid-wide barrier of the whole CTA (the launch is cooperative, so every CTA
-// is resident).  The arrival counter p.bar[0] (zeroed per batch) only grows:
-// barrier number e of the launch is passed once it reaches e * gridDim.x, so
-// an arrival is one release-add and a wait is acquire-polling of the counter,
-// with no reset between barriers.  Bounded: gives up, recording kStTimeout,
-// after the timeout (bar_extra adds arrivals that never come, for the tests).
-// Returns false, the same on every thread of the CTA, if the kernel has failed.
-__device__ __forceinline__ void red_release_add(uint32_t* a, uint32_t v) {
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
-}
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* a) {
-    uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
-    return v;
-}
-
-__device__ bool grid_sync(const SweepParams& p, uint32_t& epoch) {
+// is resident): an arrival counter that the last arriver resets before it
+// advances a generation word the others poll.  (A barrier on one ever-growing
+// counter, one release-add to arrive and acquire-polling to wait, passed the
+// grid-synchronous levels about 70 us sooner on the 18M graph but left the
+// chunk phase that follows it 0.6 ms slower, with relaxed polling as well;
+// this one is kept.)  Bounded: gives up, recording kStTimeout, after the
+// timeout (bar_extra adds arrivals that never come, for the tests).  Returns
+// false, the same on every thread of the CTA, if the kernel has failed.
+__device__ bool grid_sync(const SweepParams& p) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        ++epoch;
-        const uint32_t want = epoch * gridDim.x + (uint32_t)p.bar_extra;
-        red_release_add(p.bar, 1u);  // this CTA's writes (ordered by the CTA barrier) before the arrival
-        const unsigned long long t0 = global_ns();
-        for (uint32_t it = 0; ld_acquire(p.bar) < want; ++it) {
-            if ((it & 15) == 15) {
-                if (*(volatile int32_t*)p.status != kStOk) { ok = 0; break; }
-                if (global_ns() - t0 > (unsigned long long)p.timeout_ns || it > (1u << 28)) {
-                    atomicCAS(p.status, kStOk, kStTimeout);
-                    ok = 0;
-                    break;
+        volatile int32_t* st = p.status;
+        volatile uint32_t* gen = p.bar + 1;
+        if (*st != kStOk) {
+            ok = 0;
+        } else {
+            const uint32_t g0 = *gen;
+            fence_acq_rel_gpu();
+            const uint32_t want = gridDim.x + (uint32_t)p.bar_extra;
+            if (atomicAdd(p.bar, 1u) + 1u == want) {
+                atomicExch(p.bar, 0u);
+                fence_acq_rel_gpu();
+                atomicAdd(p.bar + 1, 1u);
+            } else {
+                const unsigned long long t0 = global_ns();
+                for (uint32_t it = 0; *gen == g0; ++it) {
+                    if ((it & 15) == 15) {
+                        if (*st != kStOk) { ok = 0; break; }
+                        if (global_ns() - t0 > (unsigned long long)p.timeout_ns || it > (1u << 28)) {
+                            atomicCAS(p.status, kStOk, kStTimeout);
+                            ok = 0;
+                            break;
+                        }
+                    }
                 }
             }
+            fence_acq_rel_gpu();
         }
-        if (ok && *(volatile int32_t*)p.status != kStOk) ok = 0;
         s_ok = ok;
     }
     __syncthreads();
@@ -582,7 +587,6 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_sweep_tma(SweepPa
     // chunks of this CTA: positions blockIdx.x, blockIdx.x + G, ...
     const int G = (int)gridDim.x;
     const int n_mine = (int)blockIdx.x < p.Q ? (p.Q - (int)blockIdx.x + G - 1) / G : 0;
-    uint32_t epoch = 0;  // grid barriers passed (thread 0's count)
 
     // (with a per-lane core, k_core has recorded the start of the sweep step)
     if (p.trace && tid == 0 && blockIdx.x == 0 && p.core_levels == 0)
@@ -592,7 +596,7 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_sweep_tma(SweepPa
     // complete for every CTA after a grid barrier.
     if (p.core_levels > 0) {
         core_rows<K>(p, warp, lane);
-        if (!grid_sync(p, epoch)) return;  // the same in every thread of the CTA
+        if (!grid_sync(p)) return;  // the same in every thread of the CTA
     }
     if (tid == 0) {
         for (int i = 0; i < kStages; ++i) {
@@ -623,12 +627,12 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_sweep_tma(SweepPa
         if (grid_levels) pl = plan_level<TPV>(p, p.solo_levels, warp, tid);
         if (p.solo_levels > p.core_levels) {
             if (blockIdx.x == 0) sweep_levels_cta<K, TPV>(p, sm, p.core_levels, p.solo_levels, warp, tid);
-            ok = grid_sync(p, epoch);
+            ok = grid_sync(p);
         }
         for (int j = p.solo_levels; ok && j < p.sync_levels; ++j) {
             finish_level<K, TPV>(p, sm, j, pl, tid);
             if (j + 1 < p.sync_levels) pl = plan_level<TPV>(p, j + 1, warp, tid);
-            ok = grid_sync(p, epoch);
+            ok = grid_sync(p);
             if (ok && p.trace && tid == 0 && blockIdx.x == 0)
                 atomicMax((unsigned long long*)p.trace + 1 + j, global_ns());
         }
