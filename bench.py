@@ -55,7 +55,7 @@ SWEEP_SOURCES = ("k_sweep_tma.cu", "iso_device.cuh", "schedule.cpp")
 # sweep options that change the kernel's memory traffic, with their defaults
 # (0 = the library's automatic choice)
 TRAFFIC_OPTS = ("threads_per_vertex", "schedule_delay", "chunk_span", "solo_width", "fuse_width", "ctas_per_sm",
-                "sweep_kernel")
+                "sweep_kernel", "core_vertices", "restrict_sweep")
 
 
 def lanes_class(k):
@@ -318,7 +318,11 @@ def main():
     ap.add_argument("--delay", type=int, default=0, help="schedule delay (TMA sweep)")
     ap.add_argument("--solo", type=int, default=0, help="top levels swept by CTA 0 alone: size limit (-1 = none)")
     ap.add_argument("--span", type=int, default=0, help="largest BFS-rank span of a sweep chunk (0 = no limit)")
+    ap.add_argument("--landmarks", type=int, default=8, help="landmarks for restricted sweeps (0 = none)")
+    ap.add_argument("--restrict", type=int, default=-1, help="restricted sweep: 1 on, 0 off, -1 autotuned")
     ap.add_argument("--pipeline", type=int, default=3, help="batches in flight (workspaces, one stream each)")
+    ap.add_argument("--no-chain", dest="chain", action="store_false",
+                    help="let batches in flight contend freely instead of starting each after the previous sweep")
     ap.add_argument("--trace", action="store_true", help="print per-step sweep times to stderr")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
@@ -347,6 +351,10 @@ def main():
     g, ch = first_on_rank0(lambda: load_graph_and_ch(spec["graph"]), dist, local)
     A = ch.arrays()
     dg = P.iso_upload_graph(ch)
+    if args.landmarks:
+        t_lm = time.perf_counter()
+        dg.add_landmarks(ch, args.landmarks)   # lower bounds for restricted sweeps
+        log(f"[bench] {args.landmarks} landmarks in {time.perf_counter() - t_lm:.1f}s")
     k = spec["k"]
     opts = dict(use_cuda_graph=1)
     tuned = None
@@ -368,6 +376,10 @@ def main():
                       (args.ctas_per_sm, "ctas_per_sm"), (args.solo, "solo_width"), (args.span, "chunk_span")):
         if flag:
             opts[key] = flag
+    if args.restrict >= 0:
+        opts["restrict_sweep"] = args.restrict
+    if not args.landmarks:
+        opts.pop("restrict_sweep", None)
     if args.trace:
         opts["record_trace"] = 1
     # batches in flight: each workspace has its own stream, so one batch's
@@ -400,13 +412,17 @@ def main():
                 sweep_ms.append(ph["sweep"])
             inflight[j] = None
 
+        prev = None
         for i in range(count):
             j = i % len(wss)
             if inflight[j] is not None:
                 finish(j)
             s, t, _, _ = batches[i % nb]
             inflight[j] = (i, time.perf_counter())
-            wss[j].submit(s, t)
+            # chained: this batch starts after the previous batch's sweep, so
+            # its upward search and core overlap that batch's emission and sort
+            wss[j].submit(s, t, after=prev if args.chain else None)
+            prev = wss[j]
         for j in range(len(wss)):
             if inflight[j] is not None:
                 finish(j)
@@ -489,16 +505,19 @@ def main():
         s_src = synth.draw_sources(g, nreq, 4000 + rank)
         s_tau = synth.draw_taus_loguniform(nreq, 600, 72000, 5000 + rank)
         sopts = {kk: v for kk, v in opts.items() if kk != "record_trace"}
-        with serving.IsoServer(dg, lanes=k, memory_fraction=0.5, max_workspaces=3, **sopts) as srv:
+        with serving.IsoServer(dg, lanes=k, workspaces=2, memory_fraction=0.5, max_workspaces=4, **sopts) as srv:
+            # a burst first: the pool grows while requests wait and memory allows
+            serving.run_poisson(srv, s_src[: nreq // 2], s_tau[: nreq // 2], np.zeros(nreq // 2))
             # the server's own capacity: every request queued at once
             _, wall0 = serving.run_poisson(srv, s_src, s_tau, np.zeros(nreq))
             capacity = nreq / wall0
             rate = 0.8 * capacity                               # 80% of the measured capacity
             s_arr = synth.poisson_arrivals(nreq, rate, 6000 + rank)
             res, wall = serving.run_poisson(srv, s_src, s_tau, s_arr)
-            nws = len(srv.workspaces)
+            nws, grown, refused = len(srv.workspaces), srv.grown, srv.refused_growth
         serving_stats = {"requests": nreq, "capacity_qps": round(capacity, 1), "offered_qps": round(rate, 1),
-                         "achieved_qps": round(nreq / wall, 1), "workspaces": nws,
+                         "achieved_qps": round(nreq / wall, 1), "workspaces": nws, "workspaces_grown": grown,
+                         "growth_refused_by_memory": refused,
                          "tau": "log-uniform [600, 72000]", "arrivals": "Poisson", **serving.latency_summary(res)}
     if rank != 0:
         if dist:
@@ -526,15 +545,16 @@ def main():
                        "m_down": int(A["down_src"].shape[0]), "levels": int(A["level_off"].shape[0] - 1),
                        "queries_per_sweep": k, "tau": list(spec["tau"]), "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (distance rows " + f"{4 * k * g.n / 1e9:.2f} GB)",
-                       "opts": opts, "batches_in_flight": len(wss)},
+                       "opts": opts, "batches_in_flight": len(wss), "chained": bool(args.chain)},
             "roofline": roof,
             "latency_ms": {"p50": round(lat[len(lat) // 2], 3), "p99": round(lat[min(len(lat) - 1,
                                                                                      int(0.99 * len(lat)))], 3)},
             "phases_ms": {key: round(statistics.mean(p[key] for p in phases), 4) for key in phases[0]},
             "serving": serving_stats,
             "autotune": None if tuned is None else {kk: v for kk, v in tuned.items() if kk != "tried"},
-            "gpu_launches": (5 if info["core_levels"] else 4) * args.steps, "e2e": e2e,
-            "sweep_shape": info}
+            "gpu_launches": (4 + (1 if info["core_levels"] else 0) + (1 if opts.get("restrict_sweep") else 0))
+            * args.steps, "e2e": e2e,
+            "sweep_shape": {**info, "skipped_chunks_last_batch": ws.skipped_chunks()}}
     clocks = clk.summary()
     if clocks:
         line["clocks"] = clocks

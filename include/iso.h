@@ -133,6 +133,25 @@ typedef struct {
 int iso_upload_graph(const iso_ch* ch, const iso_alloc* alloc, void* stream, iso_graph** out);
 void iso_free_graph(iso_graph* g);
 
+/* Landmarks for restricted sweeps: picks `count` far-apart vertices and stores,
+ * on the device, every vertex's distance from and to each of them (two PHAST
+ * queries per landmark on the host, over `ch`, which must be the hierarchy g
+ * was uploaded from).  A sweep then skips a chunk when, for every query,
+ * max over landmarks L of (d(L,v) - d(L,s), d(s,L) - d(v,L)) -- a lower bound
+ * on d(s,v) by the triangle inequality -- exceeds the query's limit for every
+ * vertex v of the chunk.  Device memory: 8 * count * n bytes.  Calling it again
+ * replaces the landmarks for workspaces created afterwards.  Errors:
+ * ISO_E_INVAL (count outside 1..ISO_MAX_LANDMARKS, another hierarchy),
+ * ISO_E_NOMEM, ISO_E_CUDA. */
+#define ISO_MAX_LANDMARKS 16
+int iso_graph_add_landmarks(iso_graph* g, const iso_ch* ch, int32_t count);
+/* The same landmarks and distances on the host (no device needed): vertices[i]
+ * is landmark i's original vertex id; fwd[i*n + v] = d(L_i, v) and
+ * bwd[i*n + v] = d(v, L_i) for original vertex v, 0xFFFFFFFF where there is
+ * no path (0xFFFFFFFE: a distance that does not fit 32 bits).  Arrays are
+ * caller-owned: vertices[count], fwd and bwd [count * n]. */
+int iso_ch_landmarks(const iso_ch* ch, int32_t count, int32_t* vertices, uint32_t* fwd, uint32_t* bwd);
+
 /* ---------------------------------------------------------------------------
  * Queries.
  * ------------------------------------------------------------------------- */
@@ -155,7 +174,7 @@ typedef struct {
     int32_t sweep_kernel;       /* 0 = auto (TMA-staged arc blocks), 1 = TMA-staged, 2 = plain loads */
     int32_t record_trace;       /* 1 = record the device time of every sweep step (iso_workspace_trace) */
     int32_t schedule_delay;     /* TMA-staged sweep: a chunk is scheduled at least this many positions
-                                   after the chunks it depends on; 0 = auto (four times the CTA count) */
+                                   after the chunks it depends on; 0 = auto (three times the CTA count) */
     int32_t solo_width;         /* TMA-staged sweep: the top levels of the hierarchy, as long as each
                                    has at most this many vertices, run in one CTA level by level
                                    (CTA barriers instead of flags between CTAs); 0 = auto (124),
@@ -172,7 +191,11 @@ typedef struct {
                                    chunk in shared memory (0 = the buffer size, 3,072); chunks with
                                    more read their arcs from global memory */
     int32_t debug_stage_deps;   /* testing only: likewise for dependency-list entries (0 = 128) */
-    int32_t reserved[1];        /* must be zero */
+    int32_t restrict_sweep;     /* TMA-staged sweep: 1 = skip the chunks that landmark lower bounds show
+                                   to be out of range for every query of the batch (Section 2's
+                                   restricted scan, Section 5's active cells); needs
+                                   iso_graph_add_landmarks; 0 = sweep everything */
+    int32_t reserved[2];        /* must be zero */
 } iso_query_opts;
 
 /* Answer k isochrone queries (source sources[i], limit taus[i]) in sweeps of
@@ -203,6 +226,15 @@ int iso_workspace_create(iso_graph* g, int32_t lanes, const iso_query_opts* opts
 #define ISO_SUBMIT_DIST 1
 int iso_submit(iso_workspace* ws, int32_t k, const int32_t* sources, const int32_t* taus, int32_t flags,
                void* stream);
+/* iso_submit whose batch starts only once the sweep of the batch last
+ * submitted on `after` (another workspace of the same graph; NULL = no wait)
+ * has finished.  Chaining each batch to the one before lets batches on
+ * several workspaces take the GPU one sweep after another -- the sweep holds
+ * every SM -- while the next batch's upward search and core overlap the
+ * previous batch's emission and sort, instead of contending with its sweep.
+ * The wait is enqueued on `stream` before the batch. */
+int iso_submit_after(iso_workspace* ws, const iso_workspace* after, int32_t k, const int32_t* sources,
+                     const int32_t* taus, int32_t flags, void* stream);
 /* Wait for the batch last submitted on ws and copy its results as iso_query
  * does (same layout, overflow and distance conventions). */
 int iso_collect(iso_workspace* ws, int64_t* out_offsets, int32_t* out_arcs, int64_t cap,
@@ -249,6 +281,8 @@ typedef struct {
     int32_t reserved[4];
 } iso_sweep_info;
 int iso_workspace_sweep_info(const iso_workspace* ws, iso_sweep_info* out);
+/* Chunks the last collected batch skipped (restricted sweep; 0 otherwise). */
+int iso_workspace_skipped_chunks(const iso_workspace* ws, int64_t* out);
 void iso_free_workspace(iso_workspace* ws);
 
 /* ---------------------------------------------------------------------------

@@ -68,7 +68,7 @@ class QueryOpts(ctypes.Structure):
                 ("schedule_delay", ctypes.c_int32), ("solo_width", ctypes.c_int32),
                 ("chunk_span", ctypes.c_int32), ("core_vertices", ctypes.c_int32),
                 ("debug_stage_arcs", ctypes.c_int32), ("debug_stage_deps", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 1)]
+                ("restrict_sweep", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class SweepInfo(ctypes.Structure):
@@ -98,6 +98,7 @@ EXPORTS = {
     "iso_query": (I32, [VP, I32, VP, VP, VP, VP, I64, VP, VP, VP]),
     "iso_workspace_create": (I32, [VP, I32, VP, VP, VP]),
     "iso_submit": (I32, [VP, I32, VP, VP, I32, VP]),
+    "iso_submit_after": (I32, [VP, VP, I32, VP, VP, I32, VP]),
     "iso_collect": (I32, [VP, VP, VP, I64, VP]),
     "iso_workspace_timings": (I32, [VP, VP]),
     "iso_free_workspace": (None, [VP]),
@@ -105,6 +106,9 @@ EXPORTS = {
     "iso_workspace_trace": (I32, [VP, VP, VP, I32]),
     "iso_workspace_sweep_info": (I32, [VP, VP]),
     "iso_collect_range": (I32, [VP, VP, I64]),
+    "iso_graph_add_landmarks": (I32, [VP, VP, I32]),
+    "iso_ch_landmarks": (I32, [VP, I32, VP, VP, VP]),
+    "iso_workspace_skipped_chunks": (I32, [VP, VP]),
     "iso_last_error": (ctypes.c_char_p, []),
     "iso_version": (ctypes.c_char_p, []),
 }
@@ -177,6 +181,16 @@ class CH:
             up_dst=arr(v.up_dst, np.int32, st.m_up), up_w=arr(v.up_w, np.int32, st.m_up),
             orig_off=arr(v.orig_off, np.int64, n + 1), orig_head=arr(v.orig_head, np.int32, st.m),
             orig_id=arr(v.orig_id, np.int32, st.m), bfs=arr(v.bfs, np.int32, n))
+
+    def landmarks(self, count: int = 8):
+        """(vertices int32[count], fwd uint32[count, n], bwd uint32[count, n]):
+        landmark ids and distances from / to them (iso_ch_landmarks)."""
+        n = self.stats()["n"]
+        v = np.zeros(count, np.int32)
+        f = np.zeros((count, n), np.uint32)
+        b = np.zeros((count, n), np.uint32)
+        _check(lib().iso_ch_landmarks(self._h, int(count), _ptr(v), _ptr(f), _ptr(b)))
+        return v, f, b
 
     def save(self, path: str):
         _check(lib().iso_save_ch(self._h, path.encode()))
@@ -254,12 +268,18 @@ class DeviceGraph:
                                       _stream_handle(self.stream), ctypes.byref(out)))
         self._h = out
         st = ch.stats()
+        self.landmarks = 0
         self.n, self.m, self.levels = st["n"], st["m"], st["levels"]
         self.m_down, self.m_up, self.max_weight = st["m_down"], st["m_up"], st["max_weight"]
 
     @property
     def handle(self):
         return self._h
+
+    def add_landmarks(self, ch: CH, count: int = 8):
+        """Landmark distances for restricted sweeps (iso_graph_add_landmarks)."""
+        _check(lib().iso_graph_add_landmarks(self._h, ch.handle, int(count)))
+        self.landmarks = int(count)
 
     def free(self):
         if self._h:
@@ -335,15 +355,21 @@ class Workspace:
         self._h = out
         self.k = 0
 
-    def submit(self, sources, taus, want_dist: bool = False):
+    def submit(self, sources, taus, want_dist: bool = False, after: "Workspace | None" = None):
+        """Enqueue a batch (iso_submit); with `after`, it starts once the sweep of
+        the batch last submitted on that workspace is done (iso_submit_after)."""
         k = int(len(sources))
         if isinstance(sources, np.ndarray) or not hasattr(sources, "data_ptr"):
             sources = np.ascontiguousarray(sources, dtype=np.int32)
         if isinstance(taus, np.ndarray) or not hasattr(taus, "data_ptr"):
             taus = np.ascontiguousarray(taus, dtype=np.int32)
         self._keep = (sources, taus)
-        _check(lib().iso_submit(self._h, k, _ptr(sources), _ptr(taus), ISO_SUBMIT_DIST if want_dist else 0,
-                                _stream_handle(self.stream)))
+        flags = ISO_SUBMIT_DIST if want_dist else 0
+        if after is not None:
+            _check(lib().iso_submit_after(self._h, after._h, k, _ptr(sources), _ptr(taus), flags,
+                                          _stream_handle(self.stream)))
+        else:
+            _check(lib().iso_submit(self._h, k, _ptr(sources), _ptr(taus), flags, _stream_handle(self.stream)))
         self.k = k
 
     def collect(self, cap: int | None = None, want_dist: bool = False, out_arcs=None, out_offsets=None,
@@ -388,6 +414,12 @@ class Workspace:
         per = int(out_bits.shape[1]) if len(out_bits.shape) == 2 else words
         _check(lib().iso_collect_range(self._h, _ptr(out_bits), per))
         return out_bits
+
+    def skipped_chunks(self) -> int:
+        """Chunks the last collected batch skipped (restricted sweep)."""
+        out = ctypes.c_int64()
+        _check(lib().iso_workspace_skipped_chunks(self._h, ctypes.byref(out)))
+        return out.value
 
     def sweep_info(self) -> dict:
         """How the sweep splits the levels and the schedule's extremes (iso_workspace_sweep_info)."""

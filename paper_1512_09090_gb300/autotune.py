@@ -9,7 +9,8 @@ picks, by query throughput:
   - the narrow-level threshold (fuse_width: leading levels below it run
     grid-synchronously, later narrow ones with a warp per vertex),
   - the CTA-0-alone width of the top levels (solo_width, used without core),
-  - the chunk span limit (chunk_span, 0 among the candidates).
+  - the chunk span limit (chunk_span, 0 among the candidates),
+  - restricted sweeps on or off (restrict_sweep), where the graph has landmarks.
 The search is coordinate descent from the library's defaults: one axis at a
 time, keeping the best value before moving on, for as many passes as the time
 budget allows.  Results are cached in a JSON file keyed by the graph's shape,
@@ -52,7 +53,7 @@ def source_hash() -> str:
 def graph_key(g: _lib.DeviceGraph) -> str:
     import torch
     dev = torch.cuda.get_device_name(g.device)
-    return f"n{g.n}-m{g.m}-down{g.m_down}-L{g.levels}-{dev}-src{source_hash()}"
+    return f"n{g.n}-m{g.m}-down{g.m_down}-L{g.levels}-lm{getattr(g, 'landmarks', 0)}-{dev}-src{source_hash()}"
 
 
 def _time_config(g, lanes, sources, taus, opts, reps):
@@ -76,14 +77,18 @@ def _time_config(g, lanes, sources, taus, opts, reps):
     return lanes * reps / el
 
 
-def axes_for(lanes: int, sms: int) -> list[tuple[str, tuple]]:
-    """The tuned options and their candidate values for a lane count (0 = the library's default)."""
-    return [("threads_per_vertex", TPV_CHOICES.get(lanes, (1,))),
+def axes_for(lanes: int, sms: int, landmarks: bool = False) -> list[tuple[str, tuple]]:
+    """The tuned options and their candidate values for a lane count (0 = the library's default);
+    restricted sweeps are a candidate where the graph has landmarks."""
+    axes = [("threads_per_vertex", TPV_CHOICES.get(lanes, (1,))),
             ("schedule_delay", tuple(r * sms for r in DELAY_ROUNDS)),
             ("core_vertices", CORE_CHOICES),
             ("fuse_width", FUSE_CHOICES),
             ("solo_width", SOLO_CHOICES),
             ("chunk_span", SPAN_CHOICES)]
+    if landmarks:
+        axes.insert(0, ("restrict_sweep", (0, 1)))
+    return axes
 
 
 def tune(g: _lib.DeviceGraph, sources, taus, lanes_choices=(64,), reps: int = 5, cache_path: str | None = None,
@@ -127,7 +132,7 @@ def tune(g: _lib.DeviceGraph, sources, taus, lanes_choices=(64,), reps: int = 5,
         cur = score(lanes, opts)
         for _ in range(passes):
             improved = False
-            for name, values in axes_for(lanes, sms):
+            for name, values in axes_for(lanes, sms, getattr(g, "landmarks", 0) > 0):
                 for v in values:
                     if time.perf_counter() - start > budget_s:
                         break
@@ -141,7 +146,8 @@ def tune(g: _lib.DeviceGraph, sources, taus, lanes_choices=(64,), reps: int = 5,
         if cur > best_qps:
             best_lanes, best_opts, best_qps = lanes, opts, cur
     result = {"lanes": best_lanes if best_lanes is not None else lanes_choices[0], **best_opts,
-              "qps": round(best_qps, 1), "axes": [a for a, _ in axes_for(best_lanes or lanes_choices[0], sms)],
+              "qps": round(best_qps, 1),
+              "axes": [a for a, _ in axes_for(best_lanes or lanes_choices[0], sms, getattr(g, "landmarks", 0) > 0)],
               "tried": tried}
     if cache_path:
         cache[ck] = result
@@ -154,4 +160,5 @@ def tune(g: _lib.DeviceGraph, sources, taus, lanes_choices=(64,), reps: int = 5,
     return result
 
 
-TUNED_KEYS = ("threads_per_vertex", "schedule_delay", "core_vertices", "fuse_width", "solo_width", "chunk_span")
+TUNED_KEYS = ("threads_per_vertex", "schedule_delay", "core_vertices", "fuse_width", "solo_width", "chunk_span",
+              "restrict_sweep")

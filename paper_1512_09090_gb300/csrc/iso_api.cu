@@ -21,6 +21,7 @@
 #include "sweep_schedule.h"
 #include "../../include/iso.h"
 #include "graph_view.h"
+#include "landmarks.h"
 
 namespace {
 
@@ -130,6 +131,10 @@ struct iso_graph {
     uint2* core_arc = nullptr;
     uint32_t* level_arc = nullptr;
     int core_cap_n = 0;
+    // landmark distances for restricted sweeps (iso_graph_add_landmarks)
+    LandmarkSet lm;
+    uint32_t* lm_fwd = nullptr;
+    uint32_t* lm_bwd = nullptr;
     int32_t* perm = nullptr;
     int32_t* pos = nullptr;
     int32_t* level_off = nullptr;
@@ -169,6 +174,11 @@ struct iso_workspace {
     int core_limit = 0;          // TMA sweep: largest per-lane core (vertices; 0: none)
     int core_levels = 0, core_n = 0;  // ... the level blocks and vertices it covers on this graph
     int stage_arc_cap = 0, stage_pred_cap = 0;  // testing: lower staging limits (0: buffer sizes)
+    bool restrict_sweep = false;  // skip chunks out of range for every lane (landmark bounds)
+    uint32_t* chunk_lo = nullptr;  // [Q * landmarks] per-chunk bounds (restricted sweep)
+    uint32_t* chunk_hi = nullptr;
+    uint8_t* skip = nullptr;       // [Q] per batch
+    int64_t skipped = 0;           // chunks skipped by the last collected batch
     iso_sweep_info info{};       // the sweep's shape (iso_workspace_sweep_info)
     bool record_trace = false;
     long long* trace = nullptr;  // device [nsched + 1]
@@ -216,6 +226,7 @@ struct iso_workspace {
     bool stale_flags = false;
     float phase_ms[4] = {};
     cudaEvent_t ev[6] = {};
+    cudaEvent_t ev_swept = nullptr;  // recorded right after the sweep of each batch (iso_submit_after)
     cudaGraphExec_t gexec[2] = {};  // indexed by want_dist
     bool graph_failed = false;
     std::vector<void*> owned;
@@ -337,6 +348,24 @@ int build_schedule(iso_workspace* ws) {
             ISO_CK(cudaMemcpyAsync(ws->sched_info, sc->info.data(), (size_t)sc->Q * sizeof(SchedChunk),
                                    cudaMemcpyHostToDevice, ws->stream));
         ISO_CK(cudaMemcpyAsync(ws->pred, sc->pred.data(), sc->pred.size() * 4, cudaMemcpyHostToDevice, ws->stream));
+        if (ws->restrict_sweep) {
+            // per-chunk landmark bounds in schedule order
+            const int c = g->lm.count;
+            std::vector<uint32_t> lo(std::max<size_t>((size_t)sc->Q * c, 1)), hi(lo.size());
+            for (int q = 0; q < sc->Q; ++q)
+                iso_landmark_chunk_bounds(g->lm, g->n, sc->info[q].v0, sc->info[q].v1, lo.data() + (size_t)q * c,
+                                          hi.data() + (size_t)q * c);
+            ws->chunk_lo = (uint32_t*)ws->alloc(lo.size() * 4);
+            ws->chunk_hi = (uint32_t*)ws->alloc(hi.size() * 4);
+            ws->skip = (uint8_t*)ws->alloc(std::max<size_t>(sc->Q, 1));
+            if (!ws->chunk_lo || !ws->chunk_hi || !ws->skip) {
+                iso::set_error("workspace: device allocation failed");
+                return ISO_E_NOMEM;
+            }
+            ISO_CK(cudaMemcpyAsync(ws->chunk_lo, lo.data(), lo.size() * 4, cudaMemcpyHostToDevice, ws->stream));
+            ISO_CK(cudaMemcpyAsync(ws->chunk_hi, hi.data(), hi.size() * 4, cudaMemcpyHostToDevice, ws->stream));
+            ISO_CK(cudaStreamSynchronize(ws->stream));  // lo/hi are freed on return
+        }
     }
     ISO_CK(cudaStreamSynchronize(ws->stream));
     return ISO_OK;
@@ -382,6 +411,13 @@ int enqueue(iso_workspace* ws, bool want_dist, bool capturing) {
     up.core_n = ws->kernel == 1 ? ws->core_n : 0;
     up.K = K; up.d = ws->d; up.upmask = ws->upmask; up.upflag = ws->upflag;
     ISO_CK(iso_launch_upward(up, K, s));
+    if (ws->skip && ws->Q > 0) {
+        SkipParams sk{};
+        sk.src = ws->src(); sk.tau = ws->tau(); sk.pos = g->pos; sk.lm_fwd = g->lm_fwd; sk.lm_bwd = g->lm_bwd;
+        sk.chunk_lo = ws->chunk_lo; sk.chunk_hi = ws->chunk_hi; sk.skip = ws->skip; sk.skipped = ws->status() + 1;
+        sk.n = g->n; sk.K = K; sk.Q = ws->Q; sk.count = g->lm.count;
+        ISO_CK(iso_launch_skip(sk, g->num_sms, s));
+    }
     ISO_CK(record(ws->ev[1], s, capturing));
 
     SweepParams sw{};
@@ -405,17 +441,21 @@ int enqueue(iso_workspace* ws, bool want_dist, bool capturing) {
     sw.core_out = ws->core_out;
     sw.stage_arc_cap = ws->stage_arc_cap;
     sw.stage_pred_cap = ws->stage_pred_cap;
+    sw.skip = ws->skip;
     if (ws->kernel == 1 && ws->core_levels > 0) ISO_CK(iso_launch_core(sw, K, s));
     if (ws->kernel == 1) ISO_CK(iso_launch_sweep_tma(sw, K, ws->tpv, ws->grid, s));
     else ISO_CK(iso_launch_sweep(sw, K, ws->tpv, ws->grid, s));
     ISO_CK(record(ws->ev[2], s, capturing));
+    ISO_CK(record(ws->ev_swept, s, capturing));
 
     EmitParams em{};
     em.orig_off = g->orig_off; em.orig_head = g->orig_head; em.orig_id = g->orig_id; em.mask = ws->mask;
     em.tail_of = g->emit_tail;
     em.status = ws->status();
     em.ecnt = ws->ecnt(); em.ebuf = ws->ebuf; em.n = g->n; em.ecap = ws->ecap;
-    ISO_CK(iso_launch_emit(em, K, g->num_sms * 8, s));
+    // four 256-thread CTAs per SM: half an SM's threads, so that the next
+    // batch's upward search (1024 threads per CTA) can be placed beside them
+    ISO_CK(iso_launch_emit(em, K, g->num_sms * 4, s));
     ISO_CK(record(ws->ev[3], s, capturing));
 
     GatherParams ga{};
@@ -482,7 +522,8 @@ int check_opts(const iso_query_opts* o) {
         if (r) { iso::set_error("iso_query_opts: reserved fields must be zero"); return ISO_E_INVAL; }
     if (o->threads_per_vertex < 0 || o->ctas_per_sm < 0 || o->fuse_width < -1 || o->barrier_timeout_ns < 0 ||
         o->debug_barrier_extra < 0 || o->schedule_delay < 0 || o->solo_width < -1 || o->chunk_span < 0 ||
-        o->core_vertices < -1 || o->debug_stage_arcs < 0 || o->debug_stage_deps < 0) {
+        o->core_vertices < -1 || o->debug_stage_arcs < 0 || o->debug_stage_deps < 0 || o->restrict_sweep < 0 ||
+        o->restrict_sweep > 1) {
         iso::set_error("iso_query_opts: negative field");
         return ISO_E_INVAL;
     }
@@ -623,12 +664,18 @@ extern "C" int iso_workspace_create(iso_graph* g, int32_t lanes, const iso_query
     // a level narrower than one chunk of ws->vpb vertices per CTA runs with a warp per vertex
     ws->narrow_width = o.fuse_width < 0 ? 0 : (o.fuse_width > 0 ? o.fuse_width : ws->grid * vpb);
     ws->record_trace = o.record_trace != 0 && ws->kernel == 1;
-    ws->sched_delay = o.schedule_delay > 0 ? o.schedule_delay : 4 * ws->grid;
+    ws->sched_delay = o.schedule_delay > 0 ? o.schedule_delay : 3 * ws->grid;
     ws->solo_width = o.solo_width < 0 ? 0 : (o.solo_width > 0 ? o.solo_width : kSoloWidth);
     ws->chunk_span = o.chunk_span;
     ws->core_limit = core_limit_of(o, g->n);
     ws->stage_arc_cap = o.debug_stage_arcs;
     ws->stage_pred_cap = o.debug_stage_deps;
+    ws->restrict_sweep = o.restrict_sweep != 0;
+    if (ws->restrict_sweep && (g->lm.count == 0 || ws->kernel != 1)) {
+        iso::set_error("iso_workspace_create: restrict_sweep needs landmarks on the graph (iso_graph_add_landmarks) "
+                       "and the TMA-staged sweep");
+        return ISO_E_INVAL;
+    }
     ws->use_graph = opts ? opts->use_cuda_graph != 0 : false;
     if (opts && opts->barrier_timeout_ns) ws->timeout_ns = opts->barrier_timeout_ns;
     ws->bar_extra = opts ? opts->debug_barrier_extra : 0;
@@ -666,6 +713,11 @@ extern "C" int iso_workspace_create(iso_graph* g, int32_t lanes, const iso_query
     }
     for (auto& e : ws->ev)
         if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); iso::set_error("iso_workspace_create: event"); return fail(ISO_E_CUDA); }
+    if (cudaEventCreateWithFlags(&ws->ev_swept, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        iso::set_error("iso_workspace_create: event");
+        return fail(ISO_E_CUDA);
+    }
     if (ws->kernel == 1 && ws->core_levels > 0) {
         ws->core_out = (uint32_t*)ws->alloc(K * (size_t)ws->core_n * 4);
         if (!ws->core_out) { iso::set_error("iso_workspace_create: device allocation failed"); return fail(ISO_E_NOMEM); }
@@ -695,6 +747,7 @@ extern "C" void iso_free_workspace(iso_workspace* ws) {
     ws->drop_graphs();
     for (auto& e : ws->ev)
         if (e) cudaEventDestroy(e);
+    if (ws->ev_swept) cudaEventDestroy(ws->ev_swept);
     for (void* p : ws->owned) ws->g->A.put(p, ws->stream);
     if (ws->h_io) cudaFreeHost(ws->h_io);
     if (ws->h_ctl) cudaFreeHost(ws->h_ctl);
@@ -703,7 +756,7 @@ extern "C" void iso_free_workspace(iso_workspace* ws) {
 
 namespace {
 int submit_impl(iso_workspace* ws, int32_t k, const int32_t* sources, const int32_t* taus, bool want_dist,
-                cudaStream_t stream) {
+                cudaStream_t stream, const iso_workspace* after = nullptr) {
     iso_graph* g = ws->g;
     if (k < 0 || k > ws->K) { iso::set_error("iso_submit: k=%d outside 0..%d", k, ws->K); return ISO_E_INVAL; }
     if (k > 0 && (!sources || !taus)) { iso::set_error("iso_submit: NULL sources or taus"); return ISO_E_INVAL; }
@@ -736,6 +789,8 @@ int submit_impl(iso_workspace* ws, int32_t k, const int32_t* sources, const int3
     ws->k = k;
     ws->want_dist = want_dist;
     ws->collected = false;
+    // the batch's kernels start once the sweep last submitted on `after` is done
+    if (after && after != ws && after->submitted) ISO_CK(cudaStreamWaitEvent(stream, after->ev_swept, 0));
     int rc = launch_batch(ws, want_dist);
     if (rc) return rc;
     ws->submitted = true;
@@ -749,6 +804,7 @@ int collect_impl(iso_workspace* ws, int64_t* out_offsets, int32_t* out_arcs, int
     for (int attempt = 0;; ++attempt) {
         ISO_CK(cudaEventSynchronize(ws->ev[5]));
         const int st = ws->h_ctl[0];
+        ws->skipped = ws->h_ctl[1];
         if (st != kStOk) ws->stale_flags = true;
         if (st == kStTimeout) { ws->submitted = false; iso::set_error("sweep: a grid barrier timed out"); return ISO_E_TIMEOUT; }
         if (st == kStBadInput) { ws->submitted = false; iso::set_error("query: a source or limit failed validation"); return ISO_E_INVAL; }
@@ -837,6 +893,15 @@ extern "C" int iso_submit(iso_workspace* ws, int32_t k, const int32_t* sources, 
     return submit_impl(ws, k, sources, taus, (flags & ISO_SUBMIT_DIST) != 0, (cudaStream_t)stream);
 }
 
+extern "C" int iso_submit_after(iso_workspace* ws, const iso_workspace* after, int32_t k, const int32_t* sources,
+                                const int32_t* taus, int32_t flags, void* stream) {
+    iso::clear_error();
+    if (!ws) { iso::set_error("iso_submit_after: NULL workspace"); return ISO_E_INVAL; }
+    if (after && after->g != ws->g) { iso::set_error("iso_submit_after: workspaces of different graphs"); return ISO_E_INVAL; }
+    if (flags & ~ISO_SUBMIT_DIST) { iso::set_error("iso_submit_after: unknown flags"); return ISO_E_INVAL; }
+    return submit_impl(ws, k, sources, taus, (flags & ISO_SUBMIT_DIST) != 0, (cudaStream_t)stream, after);
+}
+
 extern "C" int iso_collect(iso_workspace* ws, int64_t* out_offsets, int32_t* out_arcs, int64_t cap,
                            int32_t* out_dist) {
     iso::clear_error();
@@ -878,6 +943,45 @@ extern "C" int iso_workspace_sweep_info(const iso_workspace* ws, iso_sweep_info*
     return ISO_OK;
 }
 
+extern "C" int iso_workspace_skipped_chunks(const iso_workspace* ws, int64_t* out) {
+    iso::clear_error();
+    if (!ws || !out) { iso::set_error("iso_workspace_skipped_chunks: NULL argument"); return ISO_E_INVAL; }
+    *out = ws->skipped;
+    return ISO_OK;
+}
+
+extern "C" int iso_graph_add_landmarks(iso_graph* g, const iso_ch* ch, int32_t count) {
+    iso::clear_error();
+    if (!g || !ch) { iso::set_error("iso_graph_add_landmarks: NULL argument"); return ISO_E_INVAL; }
+    if (count < 1 || count > ISO_MAX_LANDMARKS) {
+        iso::set_error("iso_graph_add_landmarks: count %d outside 1..%d", count, ISO_MAX_LANDMARKS);
+        return ISO_E_INVAL;
+    }
+    if (ch->n != g->n || (int64_t)ch->down_off.back() != g->m_down) {
+        iso::set_error("iso_graph_add_landmarks: the hierarchy is not the one uploaded as this graph");
+        return ISO_E_INVAL;
+    }
+    std::lock_guard<std::mutex> lock(g->mu);
+    LandmarkSet lm;
+    try {
+        if (iso_landmarks_compute(*ch, count, &lm) != 0) { iso::set_error("iso_graph_add_landmarks: bad input"); return ISO_E_INVAL; }
+    } catch (const std::bad_alloc&) {
+        iso::set_error("iso_graph_add_landmarks: out of host memory");
+        return ISO_E_NOMEM;
+    }
+    uint32_t *f = nullptr, *b = nullptr;
+    int rc = ISO_OK;
+    if ((rc = g->upload(&f, lm.fwd.data(), lm.fwd.size())) || (rc = g->upload(&b, lm.bwd.data(), lm.bwd.size())))
+        return rc;  // a buffer already made stays owned by the graph
+    ISO_CK(cudaStreamSynchronize(g->stream));
+    if (g->lm_fwd) { g->owned.erase(std::remove(g->owned.begin(), g->owned.end(), (void*)g->lm_fwd), g->owned.end()); g->A.put(g->lm_fwd, g->stream); }
+    if (g->lm_bwd) { g->owned.erase(std::remove(g->owned.begin(), g->owned.end(), (void*)g->lm_bwd), g->owned.end()); g->A.put(g->lm_bwd, g->stream); }
+    g->lm_fwd = f;
+    g->lm_bwd = b;
+    g->lm = std::move(lm);
+    return ISO_OK;
+}
+
 extern "C" int iso_workspace_timings(const iso_workspace* ws, float* ms4) {
     if (!ws || !ms4) return ISO_E_INVAL;
     std::memcpy(ms4, ws->phase_ms, sizeof(ws->phase_ms));
@@ -895,10 +999,11 @@ bool same_config(const iso_workspace* ws, const iso_query_opts& o) {
     return ws->kernel == kernel && ws->tpv == tpv && ws->grid == ws->g->num_sms * per_sm &&
            ws->fuse_width == fuse && ws->use_graph == (o.use_cuda_graph != 0) && ws->timeout_ns == timeout &&
            ws->bar_extra == o.debug_barrier_extra && ws->record_trace == (o.record_trace != 0 && kernel == 1) &&
-           ws->sched_delay == (o.schedule_delay > 0 ? o.schedule_delay : 4 * ws->g->num_sms * per_sm) &&
+           ws->sched_delay == (o.schedule_delay > 0 ? o.schedule_delay : 3 * ws->g->num_sms * per_sm) &&
            ws->solo_width == (o.solo_width < 0 ? 0 : (o.solo_width > 0 ? o.solo_width : kSoloWidth)) &&
            ws->chunk_span == o.chunk_span && ws->core_limit == core_limit_of(o, ws->g->n) &&
-           ws->stage_arc_cap == o.debug_stage_arcs && ws->stage_pred_cap == o.debug_stage_deps;
+           ws->stage_arc_cap == o.debug_stage_arcs && ws->stage_pred_cap == o.debug_stage_deps &&
+           ws->restrict_sweep == (o.restrict_sweep != 0);
 }
 }  // namespace
 

@@ -100,6 +100,24 @@ struct SweepParams {
     // testing: stage at most this many arcs / dependency-list entries per chunk
     // (0 = the buffer sizes); larger chunks take the global-memory paths
     int stage_arc_cap, stage_pred_cap;
+    // restricted sweep: skip[q] != 0 = chunk at position q is out of range for
+    // every lane (k_skip); its rows are written kInf without gathers (nullable)
+    const uint8_t* skip;
+};
+
+// Restricted sweep: which chunks are out of range for every lane of a batch,
+// from landmark lower bounds (landmarks.h).
+struct SkipParams {
+    const int32_t* src;        // [K] original ids (-1 = idle lane)
+    const int32_t* tau;        // [K]
+    const int32_t* pos;        // [n] original id -> sweep position
+    const uint32_t* lm_fwd;    // [count * n] d(L_i, v)
+    const uint32_t* lm_bwd;    // [count * n] d(v, L_i)
+    const uint32_t* chunk_lo;  // [Q * count] min over the chunk of d(L_i, v)
+    const uint32_t* chunk_hi;  // [Q * count] max over the chunk of d(v, L_i)
+    uint8_t* skip;             // [Q]
+    int32_t* skipped;          // chunks skipped (counter)
+    int n, K, Q, count;
 };
 
 struct EmitParams {
@@ -164,6 +182,19 @@ cudaError_t iso_smem_attr_once(F* f, int bytes, std::atomic<unsigned long long>&
     return e;
 }
 
+// The highest scheduling priority of the current device (lower numbers are
+// higher), for launches that should be placed ahead of other streams' pending
+// work: a batch's upward search and core run while the previous batch's
+// emission and sort still occupy the GPU, and are placed first.
+inline int iso_high_priority() {
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return greatest;
+}
+
 // Launchers (one translation unit each); return the launch's cudaError_t.
 cudaError_t iso_launch_upward(const isod::UpParams& p, int K, cudaStream_t s);
 size_t iso_upward_table_words(size_t gcap);  // 32-bit words of one lane's global table
@@ -180,3 +211,4 @@ cudaError_t iso_launch_emit(const isod::EmitParams& p, int K, int grid, cudaStre
 cudaError_t iso_launch_sort_gather(const isod::GatherParams& p, int K, cudaStream_t s);
 cudaError_t iso_launch_dist(const isod::DistParams& p, cudaStream_t s);
 cudaError_t iso_launch_range(const isod::RangeParams& p, int K, cudaStream_t s);
+cudaError_t iso_launch_skip(const isod::SkipParams& p, int grid, cudaStream_t s);

@@ -100,6 +100,15 @@ constexpr int kCoreSmem = (kCoreMaxVertices + kCoreMaxLevels + 1) * 4;
 cudaError_t iso_launch_core(const isod::SweepParams& p, int K, cudaStream_t s) {
     static std::atomic<unsigned long long> attr{0};
     if (cudaError_t e = iso_smem_attr_once(k_core, kCoreSmem, attr)) return e;
-    k_core<<<K, kThreads, kCoreSmem, s>>>(p);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(K);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = kCoreSmem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributePriority;
+    at[0].val.priority = iso_high_priority();  // ahead of the previous batch's emission and sort
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_core, p);
 }

@@ -69,7 +69,8 @@ template <> struct MaskOf<64> { using T = unsigned long long; };
 struct Meta {
     int v0, v1;   // vertices [v0, v1)
     int abase;    // first arc index held in the stage buffer
-    int flags;    // bit 0: arcs did not fit (read them from global memory); bit 1: a warp per vertex
+    int flags;    // bit 0: arcs did not fit (read them from global memory); bit 1: a warp per vertex;
+                  // bit 2: out of range for every lane (restricted sweep): nothing staged
     int q, level; // schedule position and level block
     int pad[2];
 };
@@ -522,6 +523,21 @@ __device__ __forceinline__ void process_chunk(const SweepParams& p, const Smem& 
     const int ob = mt.v0 & ~3;
     const bool store = p.write_all || mt.level != p.last_level_block;
     const int2* arcs = (mt.flags & 1) ? p.down_arc : sm.arcs[stage] - mt.abase;
+    if (mt.flags & 4) {
+        // out of range for every lane: kInf rows, empty masks, no gathers
+        // (the bounds exclude upward labels here; a flag is cleared regardless)
+        using MaskT = typename MaskOf<K>::T;
+        const int lane = tid & 31;
+        for (int v = mt.v0 + warp; v < mt.v1; v += kConsumers / 32) {
+            if (store)
+                for (int i = lane; i < K; i += 32) p.d[(size_t)v * K + i] = kInf;
+            if (lane == 0) {
+                static_cast<MaskT*>(p.mask)[v] = (MaskT)0;
+                if (__ldcg(p.upflag + v)) { p.upflag[v] = 0; p.upmask[v] = 0ull; }
+            }
+        }
+        return;
+    }
     if (mode) {
         const int v = mt.v0 + warp;
         const bool valid = v < mt.v1;
@@ -672,19 +688,21 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_sweep_tma(SweepPa
                 const int4 c0 = n0;  // v0, v1, level, mode
                 const int4 c1 = n1;  // arc base, arcs, deps start, deps
                 const int ob = c0.x & ~3;
-                const uint32_t obytes = (uint32_t)(((c0.y + 1 - ob) * 4 + 15) & ~15);
+                // a skipped chunk needs neither its graph data nor its dependencies
+                const bool skip = p.skip && __ldg(p.skip + pos);
+                const uint32_t obytes = skip ? 0u : (uint32_t)(((c0.y + 1 - ob) * 4 + 15) & ~15);
                 const int big = c1.y > arc_cap;
-                const uint32_t abytes = big ? 0u : (uint32_t)((c1.y * 8 + 15) & ~15);
-                cur_held = c1.w <= pred_cap && p.bar_extra == 0;
-                const uint32_t pbytes = cur_held ? (uint32_t)(((c1.w + 3) & ~3) * 4) : 0u;
-                sm.meta[lane] = Meta{c0.x, c0.y, c1.x, big | (c0.w ? 2 : 0), pos, c0.z, {0, 0}};
+                const uint32_t abytes = big || skip ? 0u : (uint32_t)((c1.y * 8 + 15) & ~15);
+                cur_held = skip || (c1.w <= pred_cap && p.bar_extra == 0);
+                const uint32_t pbytes = cur_held && !skip ? (uint32_t)(((c1.w + 3) & ~3) * 4) : 0u;
+                sm.meta[lane] = Meta{c0.x, c0.y, c1.x, big | (c0.w ? 2 : 0) | (skip ? 4 : 0), pos, c0.z, {0, 0}};
                 mbar_expect_tx(&sm.full[lane], obytes + abytes + pbytes);
                 if (obytes) bulk_load(sm.offs[lane], p.down_off + ob, obytes, &sm.full[lane]);
                 if (abytes) bulk_load(sm.arcs[lane], p.down_arc + c1.x, abytes, &sm.full[lane]);
                 if (pbytes) bulk_load(sm.preds[lane], p.pred + c1.z, pbytes, &sm.full[lane]);
                 cur = t;
                 cur_pa = c1.z;
-                cur_np = c1.w;
+                cur_np = skip ? 0 : c1.w;
                 t += kStages;
                 if (t < n_mine) {
                     n0 = __ldg(p.sched_info + 2 * ((size_t)blockIdx.x + (size_t)t * G));

@@ -169,6 +169,15 @@ cudaError_t iso_launch_upward(const isod::UpParams& p, int K, cudaStream_t s) {
     const size_t smem = table_words(kSmemSlots) * 4;  // 194 KB
     static std::atomic<unsigned long long> attr{0};
     if (cudaError_t e = iso_smem_attr_once(k_upward, (int)smem, attr)) return e;
-    k_upward<<<K, kThreads, smem, s>>>(p);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(K);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributePriority;
+    at[0].val.priority = iso_high_priority();
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_upward, p);
 }

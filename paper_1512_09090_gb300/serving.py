@@ -94,16 +94,19 @@ class IsoServer:
     """Serve isochrone queries on one device graph with continuous batching.
 
     lanes: queries per batch (1..64).  workspaces: batches in flight at start
-    (None = 1).  max_workspaces: the most the pool grows to while device memory
+    (None = 1).  chain: start each batch after the sweep of the batch submitted
+    before it (iso_submit_after).  max_workspaces: the most the pool grows to while device memory
     allows (see the module docstring).  warm: run one batch on every workspace
     before it takes requests, so that no request waits for a workspace's first
     launch (CUDA-graph capture, sweep schedule upload).  Extra keyword options
     go to the workspaces (iso_query_opts fields)."""
 
     def __init__(self, g: _lib.DeviceGraph, lanes: int = 64, workspaces: int | None = None,
-                 memory_fraction: float = 0.5, max_workspaces: int = 4, warm: bool = True, **opts):
+                 memory_fraction: float = 0.5, max_workspaces: int = 4, warm: bool = True, chain: bool = True,
+                 **opts):
         import torch
         self.torch = torch
+        self.chain = chain
         self.g = g
         self.lanes = lanes
         self.opts = dict(opts)
@@ -131,6 +134,7 @@ class IsoServer:
         set-up happens here and the pool does not grow."""
         self = cls.__new__(cls)
         self.g = None
+        self.chain = False
         self.lanes = lanes
         self.max_workspaces = len(workspaces)
         self._init_state()
@@ -148,6 +152,8 @@ class IsoServer:
         self._busy = 0
         self._growing = False
         self._threads: list[threading.Thread] = []
+        self._submit_lock = threading.Lock()
+        self._last_ws = None
 
     def _new_workspace(self):
         ws = _lib.Workspace(self.g, self.lanes, **self.opts)
@@ -247,7 +253,15 @@ class IsoServer:
             srcs = np.fromiter((p.source for p in batch), np.int32, len(batch))
             taus = np.fromiter((p.tau for p in batch), np.int32, len(batch))
             try:
-                ws.submit(srcs, taus)
+                with self._submit_lock:
+                    # chained to the batch submitted last: sweeps take the GPU one
+                    # after another while the next batch's upward search and core
+                    # overlap the previous batch's emission and sort
+                    prev, self._last_ws = self._last_ws, ws
+                    if prev is not None and prev is not ws and self.chain:
+                        ws.submit(srcs, taus, after=prev)
+                    else:
+                        ws.submit(srcs, taus)
                 b.off, b.arcs, _ = ws.collect()
             except Exception as e:  # reported to every request of the batch
                 b.error = e

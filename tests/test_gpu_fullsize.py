@@ -105,3 +105,25 @@ def test_fullsize_labels_sampled_against_oracle(big):
     off, arcs, dist = P.iso_query(dg, srcs, taus, want_dist=True)
     _, _, o_dist = oracle.query_batch(g.n, g.tail, g.head, g.weight, srcs, taus, want_dist=True, threads=2)
     assert np.array_equal(dist, o_dist)
+
+
+def test_fullsize_restricted_sweep(big):
+    # one source per launch with small limits, and a 64-lane batch, with chunks
+    # skipped by landmark bounds
+    g, dg = big
+    ch = chcache.workload_graph_and_ch("grid18m")[1]
+    dg.add_landmarks(ch, 8)
+    srcs = synth.draw_sources(g, 4, 10_005)
+    taus = np.array([3600, 5000, 9000, 20000], np.int32)
+    for i in range(4):
+        ws = P.Workspace(dg, 1, use_cuda_graph=1, restrict_sweep=1)
+        ws.submit(srcs[i:i + 1], taus[i:i + 1])
+        off, arcs, _ = ws.collect()
+        assert ws.skipped_chunks() > 0
+        ws.free()
+        _against_oracle(g, srcs[i:i + 1], taus[i:i + 1], off, arcs, [0])
+    k = 64
+    srcs = synth.draw_sources(g, k, 10_006)
+    taus = synth.draw_taus_uniform(k, 3600, 72000, 20_006)
+    off, arcs, _ = _batch(dg, srcs, taus, restrict_sweep=1)
+    _against_oracle(g, srcs, taus, off, arcs, [0, 17, 38, 63, int(np.argmin(taus))])

@@ -375,3 +375,75 @@ def test_vertices_in_range_bitsets(k):
     assert np.all(got[:, words:] == -1)
     assert np.array_equal(got[:, :words].view(np.uint32), bits)
     ws.free()
+
+
+def test_chained_batches_on_two_workspaces():
+    # iso_submit_after: each batch starts after the previous batch's sweep on
+    # the other workspace; results equal those of independent queries
+    g, dg = dev_graph("grid1k")
+    wss = [P.Workspace(dg, 16, use_cuda_graph=1, stream=torch.cuda.Stream()) for _ in range(2)]
+    batches = [(synth.draw_sources(g, 16, 120 + b), synth.draw_taus_uniform(16, 0, 60000, 140 + b)) for b in range(6)]
+    got, prev = {}, None
+    for b, (s, t) in enumerate(batches):
+        ws = wss[b % 2]
+        if b >= 2:
+            got[b - 2] = ws.collect()
+        ws.submit(s, t, after=prev)
+        prev = ws
+    got[4] = wss[0].collect()
+    got[5] = wss[1].collect()
+    for b, (s, t) in enumerate(batches):
+        off, arcs, _ = P.iso_query(dg, s, t)
+        assert np.array_equal(got[b][0], off) and np.array_equal(got[b][1], arcs), b
+    for ws in wss:
+        ws.free()
+
+
+_LM = {}
+
+
+def lm_graph(name):
+    """A device graph of the workload with landmarks for restricted sweeps."""
+    if name not in _LM:
+        g, ch = workload(name)
+        dg = P.iso_upload_graph(ch)
+        dg.add_landmarks(ch, 8)
+        _LM[name] = (g, dg)
+    return _LM[name]
+
+
+@pytest.mark.parametrize("k,tmax", [(1, 3000), (1, 20000), (3, 8000), (16, 5000), (64, 60000)])
+def test_restricted_sweep(k, tmax):
+    # chunks that landmark bounds show out of range for every lane are skipped;
+    # the answers stay exact (lists and distances)
+    g, dg = lm_graph("grid1k")
+    srcs = synth.draw_sources(g, k, 150 + k)
+    taus = synth.draw_taus_uniform(k, 0, tmax, 160 + k)
+    ws = P.Workspace(dg, k, restrict_sweep=1, use_cuda_graph=1)
+    ws.submit(srcs, taus, want_dist=True)
+    off, arcs, dist = ws.collect(want_dist=True)
+    skipped = ws.skipped_chunks()
+    chunks = ws.sweep_info()["chunks"]
+    ws.free()
+    o_off, o_arcs, o_dist = oracle.query_batch(g.n, g.tail, g.head, g.weight, srcs, taus, want_dist=True, threads=8)
+    assert np.array_equal(off, o_off) and np.array_equal(arcs, o_arcs) and np.array_equal(dist, o_dist)
+    if tmax <= 8000:
+        assert skipped > chunks // 2        # small limits: most of the map is skipped
+    assert 0 <= skipped <= chunks
+
+
+def test_restricted_sweep_errors_and_reuse():
+    g, dg = dev_graph("grid64")               # no landmarks on this graph
+    with pytest.raises(P.IsoError):
+        P.Workspace(dg, 4, restrict_sweep=1)
+    g, dg = lm_graph("grid1k")
+    srcs = synth.draw_sources(g, 16, 171)
+    taus = synth.draw_taus_uniform(16, 0, 6000, 172)
+    # two batches in a row on one workspace, then without restriction: all equal
+    ws = P.Workspace(dg, 16, restrict_sweep=1)
+    for _ in range(2):
+        ws.submit(srcs, taus)
+        off, arcs, _ = ws.collect()
+    ws.free()
+    o2, a2, _ = P.iso_query(dg, srcs, taus)
+    assert np.array_equal(off, o2) and np.array_equal(arcs, a2)
