@@ -36,6 +36,8 @@ WORKLOADS = {
     "grid18m_k16": dict(graph="grid18m", k=16, tau=("fixed", 36000)),
     # 18M-vertex graph, one source per launch
     "grid18m_k1": dict(graph="grid18m", k=1, tau=("uniform", 3600, 72000)),
+    # 18M-vertex graph, one source per launch, limit 3,600 (a small range: restricted sweeps)
+    "grid18m_k1_tau3600": dict(graph="grid18m", k=1, tau=("fixed", 3600)),
     # 18M-vertex graph, uneven limits, queries per sweep chosen by the autotuner among 16, 32, 64
     "grid18m_kauto": dict(graph="grid18m", k=64, lanes=(16, 32, 64), tau=("uniform", 3600, 72000)),
     "grid4m_k64": dict(graph="grid4m", k=64, tau=("uniform", 3600, 72000)),
@@ -320,7 +322,7 @@ def main():
     ap.add_argument("--span", type=int, default=0, help="largest BFS-rank span of a sweep chunk (0 = no limit)")
     ap.add_argument("--landmarks", type=int, default=8, help="landmarks for restricted sweeps (0 = none)")
     ap.add_argument("--restrict", type=int, default=-1, help="restricted sweep: 1 on, 0 off, -1 autotuned")
-    ap.add_argument("--pipeline", type=int, default=3, help="batches in flight (workspaces, one stream each)")
+    ap.add_argument("--pipeline", type=int, default=2, help="batches in flight (workspaces, one stream each)")
     ap.add_argument("--no-chain", dest="chain", action="store_false",
                     help="let batches in flight contend freely instead of starting each after the previous sweep")
     ap.add_argument("--trace", action="store_true", help="print per-step sweep times to stderr")

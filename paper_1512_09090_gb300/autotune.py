@@ -38,6 +38,7 @@ CORE_CHOICES = (0, 20000, -1)
 FUSE_CHOICES = (0, -1)
 SOLO_CHOICES = (0, -1)
 SPAN_CHOICES = (0, 10000)
+COMBO_SPANS = (4096, 16384)  # chunk spans tried together with restricted sweeps
 _CSRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc")
 
 
@@ -143,6 +144,15 @@ def tune(g: _lib.DeviceGraph, sources, taus, lanes_choices=(64,), reps: int = 5,
                         opts, cur, improved = cand, q, True
             if not improved:
                 break
+        # restricted sweeps skip more with spatially compact chunks: try the pair
+        if getattr(g, "landmarks", 0) > 0:
+            for span in COMBO_SPANS:
+                if time.perf_counter() - start > budget_s:
+                    break
+                cand = {**opts, "restrict_sweep": 1, "chunk_span": span}
+                q = score(lanes, cand)
+                if q > cur * 1.005:
+                    opts, cur = cand, q
         if cur > best_qps:
             best_lanes, best_opts, best_qps = lanes, opts, cur
     result = {"lanes": best_lanes if best_lanes is not None else lanes_choices[0], **best_opts,

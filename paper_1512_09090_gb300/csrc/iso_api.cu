@@ -464,6 +464,7 @@ int enqueue(iso_workspace* ws, bool want_dist, bool capturing) {
     ga.status = ws->status();
     ga.key_bits = 1;
     while (ga.key_bits < 31 && (int64_t(1) << ga.key_bits) < g->m) ++ga.key_bits;
+    ga.m = g->m;
     ISO_CK(iso_launch_sort_gather(ga, K, s));
     if (want_dist) {
         DistParams dp{};

@@ -140,6 +140,7 @@ struct GatherParams {
     int64_t* out_off;          // [K+1]
     int k, ecap;
     int key_bits;              // bits needed for arc ids
+    int64_t m;                 // arc ids are in [0, m)
     const int32_t* status;     // batch status: nothing is written once it is not kStOk
 };
 

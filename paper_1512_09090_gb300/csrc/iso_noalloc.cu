@@ -202,6 +202,7 @@ extern "C" int iso_query_noalloc(iso_graph* g, int32_t k, const int32_t* sources
     ga.status = ctl;
     ga.key_bits = 1;
     while (ga.key_bits < 31 && (int64_t(1) << ga.key_bits) < gv.m) ++ga.key_bits;
+    ga.m = gv.m;
     if ((e = iso_launch_sort_gather(ga, kLanes, stream)) != cudaSuccess)
         return fail_enqueued(ISO_E_CUDA, "sort launch", e, stream);
 

@@ -7,9 +7,9 @@
 // atomicAdd per warp: __ballot_sync gives the warp's members for that lane and
 // __popc of the lower lanes gives each member's slot.
 //
-// Then one CTA per lane sorts its ids ascending (bitonic network, in shared
-// memory when it fits, else in global memory) and writes them to the
-// contiguous output at the lane's offset; CTA 0 also writes the offsets.
+// Then k_sort_gather sorts each lane's ids ascending (bucket sort in shared
+// memory, four CTAs per lane) and writes them to the contiguous output at the
+// lane's offset; CTA 0 also writes the offsets.
 #include "iso_device.cuh"
 
 namespace {
@@ -23,7 +23,7 @@ template <> struct MaskOf<64> { using T = unsigned long long; };
 
 constexpr int kEmitThreads = 256;
 constexpr int kSortThreads = 1024;
-constexpr int kSortSmem = 32768;  // ids bucketed in shared memory (128 KB)
+constexpr int kSortSmem = 16384;  // ids bucketed in shared memory (64 KB): two sorting CTAs fit an SM
 
 __device__ __forceinline__ unsigned long long warp_or(unsigned long long x) {
     const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)x);
@@ -88,74 +88,51 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(EmitParams p) {
     }
 }
 
-// In-place ascending bitonic sort of s[0..n2), n2 a power of two, one CTA.
-__device__ void bitonic(int32_t* s, int n2) {
-    for (int k = 2; k <= n2; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < n2; i += blockDim.x) {
-                const int ij = i ^ j;
-                if (ij > i) {
-                    const int32_t x = s[i], y = s[ij];
-                    const bool up = (i & k) == 0;
-                    if ((x > y) == up) { s[i] = y; s[ij] = x; }
-                }
-            }
-            __syncthreads();
-        }
-    }
-}
-
-// One CTA per lane.  Ids are distinct and below 2^key_bits, so the list is
-// split by its top bits into about cnt/4 buckets (histogram, scan, scatter);
-// buckets are then sorted on their own: small ones by one thread each
-// (insertion sort), any bucket above kSmallBucket ids by the whole CTA
-// (bitonic network in the lane's global scratch).  Concatenated buckets are
-// the sorted list.  CTA 0 also writes the offsets of all lanes.
-constexpr int kMaxBuckets = 8192;
+// kParts CTAs per lane.  Ids are distinct and in [0, m); CTA (lane, part)
+// takes the ids of the part-th of kParts equal slices of [0, m) (their count
+// and the counts of the slices before it come from one pass over the lane's
+// list), so the parts' sorted lists are consecutive pieces of the lane's
+// sorted list.  A part is split into about cnt/4 equal buckets of its slice
+// (histogram, scan, scatter into shared memory); buckets are then sorted on
+// their own: small ones by one thread each (insertion sort), any bucket above
+// kSmallBucket ids by the whole CTA (every id's rank by counting the smaller
+// ones in its bucket, written straight to its place).  CTA 0 also writes the
+// offsets of all lanes.  A lane one of whose parts would not fit shared memory
+// is sorted by its part-0 CTA alone with the list in global memory (the other
+// parts of that lane return).
+constexpr int kMaxBuckets = 4096;
 constexpr int kSmallBucket = 64;
+constexpr int kMaxBigBuckets = 256;  // big buckets listed for the whole-CTA ranking
+constexpr int kParts = 4;
 
-__global__ void __launch_bounds__(kSortThreads) k_sort_gather(GatherParams p) {
-    extern __shared__ int32_t sbuf[];
-    int32_t* s_hist = sbuf + kSortSmem;           // [kMaxBuckets + 1]
-    int32_t* s_cur = s_hist + kMaxBuckets + 1;    // [kMaxBuckets]
-    __shared__ long long s_off;
-    __shared__ int s_nbig, s_big[256];
-    const int lane = blockIdx.x;
-    if (*(volatile const int32_t*)p.status != kStOk) return;  // failed batch: the host reports it
-    if (threadIdx.x == 0) {
-        long long off = 0;
-        for (int i = 0; i < lane; ++i) off += min(p.ecnt[i], p.ecap);
-        s_off = off;
-        s_nbig = 0;
-        if (lane == 0) {
-            long long o = 0;
-            p.out_off[0] = 0;
-            for (int i = 0; i < p.k; ++i) { o += min(p.ecnt[i], p.ecap); p.out_off[i + 1] = o; }
-        }
-    }
-    __syncthreads();
-    if (lane >= p.k) return;
-    const int cnt = min(p.ecnt[lane], p.ecap);
-    if (cnt == 0) return;
-    const int32_t* seg = p.ebuf + (size_t)lane * p.ecap;
-    int32_t* tmp = p.tmp + (size_t)lane * p.ecap;
-    int32_t* out = p.out + s_off;
-    int32_t* B = cnt <= kSortSmem ? sbuf : tmp;     // bucketed copy of the list
+// Sorts the ids x of src[0..src_cnt) with lo <= x < hi (cnt of them) into
+// out[0..cnt): bucketed into B[0..cnt) by equal slices of [lo, hi) (about four
+// ids per bucket), small buckets sorted in place and copied, big buckets
+// ranked straight into out.
+__device__ void bucket_sort(const int32_t* src, int src_cnt, int32_t* B, int cnt, int32_t* out, int64_t lo,
+                            int64_t hi, int32_t* s_hist, int32_t* s_cur) {
+    __shared__ int s_part[kSortThreads];
+    __shared__ int s_nbig, s_big[kMaxBigBuckets];
     int lg = 0;
     while ((1 << lg) < kMaxBuckets && (4 << lg) < cnt) ++lg;
     const int nb = 1 << lg;
-    const int shift = max(0, p.key_bits - lg);
-    for (int b = threadIdx.x; b <= nb; b += blockDim.x) s_hist[b] = 0;
+    const uint64_t span = (uint64_t)(hi - lo);
+    auto bucket_of = [&](int32_t x) { return (int)((uint64_t)(x - lo) * (uint64_t)nb / span); };
+    auto mine = [&](int32_t x) { return x >= lo && x < hi; };
+    for (int bb = threadIdx.x; bb <= nb; bb += blockDim.x) s_hist[bb] = 0;
+    if (threadIdx.x == 0) s_nbig = 0;
     __syncthreads();
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) atomicAdd(&s_hist[min(seg[i] >> shift, nb - 1)], 1);
+    for (int i = threadIdx.x; i < src_cnt; i += blockDim.x) {
+        const int32_t x = src[i];
+        if (mine(x)) atomicAdd(&s_hist[bucket_of(x)], 1);
+    }
     __syncthreads();
-    // exclusive scan of the nb counts (nb <= 8192 = 8 per thread)
+    // exclusive scan of the nb counts (nb <= kMaxBuckets, a few per thread)
     {
-        __shared__ int s_part[kSortThreads];
         const int per = (nb + blockDim.x - 1) / blockDim.x;
         const int b0 = threadIdx.x * per;
         int sum = 0;
-        for (int b = b0; b < min(b0 + per, nb); ++b) sum += s_hist[b];
+        for (int bb = b0; bb < min(b0 + per, nb); ++bb) sum += s_hist[bb];
         s_part[threadIdx.x] = sum;
         __syncthreads();
         for (int o = 1; o < (int)blockDim.x; o <<= 1) {
@@ -165,60 +142,102 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_gather(GatherParams p) {
             __syncthreads();
         }
         int acc = s_part[threadIdx.x] - sum;
-        for (int b = b0; b < min(b0 + per, nb); ++b) {
-            const int c = s_hist[b];
-            s_hist[b] = acc;
-            s_cur[b] = acc;
+        for (int bb = b0; bb < min(b0 + per, nb); ++bb) {
+            const int c = s_hist[bb];
+            s_hist[bb] = acc;
+            s_cur[bb] = acc;
             acc += c;
         }
         if (threadIdx.x == 0) s_hist[nb] = cnt;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-        const int32_t x = seg[i];
-        B[atomicAdd(&s_cur[min(x >> shift, nb - 1)], 1)] = x;
+    for (int i = threadIdx.x; i < src_cnt; i += blockDim.x) {
+        const int32_t x = src[i];
+        if (mine(x)) B[atomicAdd(&s_cur[bucket_of(x)], 1)] = x;
     }
     __syncthreads();
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        const int lo = s_hist[b], hi = s_hist[b + 1];
-        if (hi - lo > kSmallBucket) {
+    for (int bb = threadIdx.x; bb < nb; bb += blockDim.x) {
+        const int blo = s_hist[bb], bhi = s_hist[bb + 1];
+        if (bhi - blo > kSmallBucket) {
             const int q = atomicAdd(&s_nbig, 1);
-            if (q < 256) s_big[q] = b;
+            if (q < kMaxBigBuckets) s_big[q] = bb;
             continue;
         }
-        for (int i = lo + 1; i < hi; ++i) {
+        for (int i = blo + 1; i < bhi; ++i) {
             const int32_t x = B[i];
             int j = i - 1;
-            while (j >= lo && B[j] > x) { B[j + 1] = B[j]; --j; }
+            while (j >= blo && B[j] > x) { B[j + 1] = B[j]; --j; }
             B[j + 1] = x;
         }
+        for (int i = blo; i < bhi; ++i) out[i] = B[i];
     }
     __syncthreads();
+    // big buckets: the whole CTA, each id's place is the count of smaller ids
+    // (the list of them, or every bucket if it overflowed)
     const int nbig = s_nbig;
-    if (nbig > 256) {
-        // too many large buckets: sort the whole list with one network in scratch
-        int n2 = 1;
-        while (n2 < cnt) n2 <<= 1;
-        int32_t* g = const_cast<int32_t*>(seg);
-        for (int i = threadIdx.x; i < n2; i += blockDim.x) g[i] = i < cnt ? B[i] : INT32_MAX;
-        __syncthreads();
-        bitonic(g, n2);
-        for (int i = threadIdx.x; i < cnt; i += blockDim.x) out[i] = g[i];
+    for (int t = 0; t < (nbig <= kMaxBigBuckets ? nbig : nb); ++t) {
+        const int bb = nbig <= kMaxBigBuckets ? s_big[t] : t;
+        const int blo = s_hist[bb], bhi = s_hist[bb + 1];
+        if (bhi - blo <= kSmallBucket) continue;
+        for (int i = blo + threadIdx.x; i < bhi; i += blockDim.x) {
+            const int32_t x = B[i];
+            int r = 0;
+            for (int j = blo; j < bhi; ++j) r += B[j] < x;
+            out[blo + r] = x;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_gather(GatherParams p) {
+    extern __shared__ int32_t sbuf[];
+    int32_t* s_hist = sbuf + kSortSmem;           // [kMaxBuckets + 1]
+    int32_t* s_cur = s_hist + kMaxBuckets + 1;    // [kMaxBuckets]
+    __shared__ long long s_off;
+    __shared__ int s_pc[kParts];
+    const int lane = blockIdx.x / kParts, part = blockIdx.x % kParts;
+    if (*(volatile const int32_t*)p.status != kStOk) return;  // failed batch: the host reports it
+    if (threadIdx.x == 0) {
+        long long off = 0;
+        for (int i = 0; i < lane; ++i) off += min(p.ecnt[i], p.ecap);
+        s_off = off;
+        if (blockIdx.x == 0) {
+            long long o = 0;
+            p.out_off[0] = 0;
+            for (int i = 0; i < p.k; ++i) { o += min(p.ecnt[i], p.ecap); p.out_off[i + 1] = o; }
+        }
+    }
+    if (threadIdx.x < kParts) s_pc[threadIdx.x] = 0;
+    __syncthreads();
+    if (lane >= p.k) return;
+    const int cnt = min(p.ecnt[lane], p.ecap);
+    if (cnt == 0) return;
+    const int32_t* seg = p.ebuf + (size_t)lane * p.ecap;
+    int32_t* out = p.out + s_off;
+    const int64_t m = p.m > 0 ? p.m : 1;
+    // part q holds [slice(q), slice(q + 1)), i.e. exactly the ids x with x * kParts / m == q
+    auto slice = [&](int q) { return (m * q + kParts - 1) / kParts; };
+    {
+        int c[kParts] = {0, 0, 0, 0};
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x)
+            c[min((int)((int64_t)seg[i] * kParts / m), kParts - 1)]++;
+        for (int q = 0; q < kParts; ++q)
+            if (c[q]) atomicAdd(&s_pc[q], c[q]);
+    }
+    __syncthreads();
+    bool lane_mode = false;
+    int below = 0;
+    for (int q = 0; q < kParts; ++q) {
+        lane_mode = lane_mode || s_pc[q] > kSortSmem;
+        if (q < part) below += s_pc[q];
+    }
+    if (!lane_mode) {
+        const int my = s_pc[part];
+        if (my > 0) bucket_sort(seg, cnt, sbuf, my, out + below, slice(part), slice(part + 1), s_hist, s_cur);
         return;
     }
-    for (int t = 0; t < nbig; ++t) {
-        const int b = s_big[t];
-        const int lo = s_hist[b], c = s_hist[b + 1] - lo;
-        int n2 = 1;
-        while (n2 < c) n2 <<= 1;
-        int32_t* g = const_cast<int32_t*>(seg);     // the input list is no longer needed
-        for (int i = threadIdx.x; i < n2; i += blockDim.x) g[i] = i < c ? B[lo + i] : INT32_MAX;
-        __syncthreads();
-        bitonic(g, n2);
-        for (int i = threadIdx.x; i < c; i += blockDim.x) B[lo + i] = g[i];
-        __syncthreads();
-    }
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) out[i] = B[i];
+    if (part != 0) return;
+    // the whole lane in one CTA, bucketed in global scratch
+    bucket_sort(seg, cnt, p.tmp + (size_t)lane * p.ecap, cnt, out, 0, m, s_hist, s_cur);
 }
 
 __global__ void k_dist(DistParams p) {
@@ -283,7 +302,7 @@ cudaError_t iso_launch_sort_gather(const isod::GatherParams& p, int K, cudaStrea
     const int smem = (kSortSmem + 2 * kMaxBuckets + 1) * 4;
     static std::atomic<unsigned long long> attr{0};
     if (cudaError_t e = iso_smem_attr_once(k_sort_gather, smem, attr)) return e;
-    k_sort_gather<<<K, kSortThreads, smem, s>>>(p);
+    k_sort_gather<<<K * kParts, kSortThreads, smem, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -524,17 +524,22 @@ __device__ __forceinline__ void process_chunk(const SweepParams& p, const Smem& 
     const bool store = p.write_all || mt.level != p.last_level_block;
     const int2* arcs = (mt.flags & 1) ? p.down_arc : sm.arcs[stage] - mt.abase;
     if (mt.flags & 4) {
-        // out of range for every lane: kInf rows, empty masks, no gathers
-        // (the bounds exclude upward labels here; a flag is cleared regardless)
+        // out of range for every lane: kInf rows, empty masks, no gathers, a
+        // thread per vertex (the bounds exclude upward labels here; a flag is
+        // cleared regardless)
         using MaskT = typename MaskOf<K>::T;
-        const int lane = tid & 31;
-        for (int v = mt.v0 + warp; v < mt.v1; v += kConsumers / 32) {
-            if (store)
-                for (int i = lane; i < K; i += 32) p.d[(size_t)v * K + i] = kInf;
-            if (lane == 0) {
-                static_cast<MaskT*>(p.mask)[v] = (MaskT)0;
-                if (__ldcg(p.upflag + v)) { p.upflag[v] = 0; p.upmask[v] = 0ull; }
+        for (int v = mt.v0 + tid; v < mt.v1; v += kConsumers) {
+            if (store) {
+                if constexpr (K >= 4) {
+#pragma unroll
+                    for (int i = 0; i < K / 4; ++i)
+                        reinterpret_cast<uint4*>(p.d + (size_t)v * K)[i] = make_uint4(kInf, kInf, kInf, kInf);
+                } else {
+                    for (int i = 0; i < K; ++i) p.d[(size_t)v * K + i] = kInf;
+                }
             }
+            static_cast<MaskT*>(p.mask)[v] = (MaskT)0;
+            if (__ldcg(p.upflag + v)) { p.upflag[v] = 0; p.upmask[v] = 0ull; }
         }
         return;
     }
