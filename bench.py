@@ -57,7 +57,7 @@ SWEEP_SOURCES = ("k_sweep_tma.cu", "iso_device.cuh", "schedule.cpp")
 # sweep options that change the kernel's memory traffic, with their defaults
 # (0 = the library's automatic choice)
 TRAFFIC_OPTS = ("threads_per_vertex", "schedule_delay", "chunk_span", "solo_width", "fuse_width", "ctas_per_sm",
-                "sweep_kernel", "core_vertices", "restrict_sweep")
+                "sweep_kernel", "core_vertices", "restrict_sweep", "fused_emission")
 
 
 def lanes_class(k):
@@ -322,6 +322,7 @@ def main():
     ap.add_argument("--span", type=int, default=0, help="largest BFS-rank span of a sweep chunk (0 = no limit)")
     ap.add_argument("--landmarks", type=int, default=8, help="landmarks for restricted sweeps (0 = none)")
     ap.add_argument("--restrict", type=int, default=-1, help="restricted sweep: 1 on, 0 off, -1 autotuned")
+    ap.add_argument("--fused", type=int, default=-1, help="fused emission: 1 on, 0 off, -1 autotuned")
     ap.add_argument("--pipeline", type=int, default=2, help="batches in flight (workspaces, one stream each)")
     ap.add_argument("--no-chain", dest="chain", action="store_false",
                     help="let batches in flight contend freely instead of starting each after the previous sweep")
@@ -380,6 +381,8 @@ def main():
             opts[key] = flag
     if args.restrict >= 0:
         opts["restrict_sweep"] = args.restrict
+    if args.fused >= 0:
+        opts["fused_emission"] = args.fused
     if not args.landmarks:
         opts.pop("restrict_sweep", None)
     if args.trace:
@@ -554,7 +557,8 @@ def main():
             "phases_ms": {key: round(statistics.mean(p[key] for p in phases), 4) for key in phases[0]},
             "serving": serving_stats,
             "autotune": None if tuned is None else {kk: v for kk, v in tuned.items() if kk != "tried"},
-            "gpu_launches": (4 + (1 if info["core_levels"] else 0) + (1 if opts.get("restrict_sweep") else 0))
+            "gpu_launches": (4 + (1 if info["core_levels"] else 0) + (1 if opts.get("restrict_sweep") else 0)
+                             - (1 if opts.get("fused_emission") else 0))
             * args.steps, "e2e": e2e,
             "sweep_shape": {**info, "skipped_chunks_last_batch": ws.skipped_chunks()}}
     clocks = clk.summary()

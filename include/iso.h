@@ -195,7 +195,11 @@ typedef struct {
                                    to be out of range for every query of the batch (Section 2's
                                    restricted scan, Section 5's active cells); needs
                                    iso_graph_add_landmarks; 0 = sweep everything */
-    int32_t reserved[2];        /* must be zero */
+    int32_t fused_emission;     /* TMA-staged sweep: 1 = the sweep emits the isochrone edges itself
+                                   (Section 5: each input arc is checked at its later-swept endpoint
+                                   once that vertex is final), with no separate emission pass;
+                                   0 = a separate pass over all arcs after the sweep */
+    int32_t reserved[1];        /* must be zero */
 } iso_query_opts;
 
 /* Answer k isochrone queries (source sources[i], limit taus[i]) in sweeps of

@@ -68,7 +68,8 @@ class QueryOpts(ctypes.Structure):
                 ("schedule_delay", ctypes.c_int32), ("solo_width", ctypes.c_int32),
                 ("chunk_span", ctypes.c_int32), ("core_vertices", ctypes.c_int32),
                 ("debug_stage_arcs", ctypes.c_int32), ("debug_stage_deps", ctypes.c_int32),
-                ("restrict_sweep", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("restrict_sweep", ctypes.c_int32), ("fused_emission", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
 class SweepInfo(ctypes.Structure):

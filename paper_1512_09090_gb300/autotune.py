@@ -10,7 +10,8 @@ picks, by query throughput:
     grid-synchronously, later narrow ones with a warp per vertex),
   - the CTA-0-alone width of the top levels (solo_width, used without core),
   - the chunk span limit (chunk_span, 0 among the candidates),
-  - restricted sweeps on or off (restrict_sweep), where the graph has landmarks.
+  - restricted sweeps on or off (restrict_sweep), where the graph has landmarks,
+  - emission fused into the sweep or as a separate pass (fused_emission).
 The search is coordinate descent from the library's defaults: one axis at a
 time, keeping the best value before moving on, for as many passes as the time
 budget allows.  Results are cached in a JSON file keyed by the graph's shape,
@@ -81,7 +82,8 @@ def _time_config(g, lanes, sources, taus, opts, reps):
 def axes_for(lanes: int, sms: int, landmarks: bool = False) -> list[tuple[str, tuple]]:
     """The tuned options and their candidate values for a lane count (0 = the library's default);
     restricted sweeps are a candidate where the graph has landmarks."""
-    axes = [("threads_per_vertex", TPV_CHOICES.get(lanes, (1,))),
+    axes = [("fused_emission", (0, 1)),
+            ("threads_per_vertex", TPV_CHOICES.get(lanes, (1,))),
             ("schedule_delay", tuple(r * sms for r in DELAY_ROUNDS)),
             ("core_vertices", CORE_CHOICES),
             ("fuse_width", FUSE_CHOICES),
@@ -171,4 +173,4 @@ def tune(g: _lib.DeviceGraph, sources, taus, lanes_choices=(64,), reps: int = 5,
 
 
 TUNED_KEYS = ("threads_per_vertex", "schedule_delay", "core_vertices", "fuse_width", "solo_width", "chunk_span",
-              "restrict_sweep")
+              "restrict_sweep", "fused_emission")

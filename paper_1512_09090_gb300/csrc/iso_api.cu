@@ -131,6 +131,10 @@ struct iso_graph {
     uint2* core_arc = nullptr;
     uint32_t* level_arc = nullptr;
     int core_cap_n = 0;
+    // fused emission: input arcs by their later-swept endpoint {other endpoint, arc id}
+    uint32_t* emit_off = nullptr;   // [n+1]
+    int2* emit_ent = nullptr;
+    int64_t dummy_arcs = 0;         // dummy downward arcs added for one-way input arcs
     // landmark distances for restricted sweeps (iso_graph_add_landmarks)
     LandmarkSet lm;
     uint32_t* lm_fwd = nullptr;
@@ -175,6 +179,7 @@ struct iso_workspace {
     int core_levels = 0, core_n = 0;  // ... the level blocks and vertices it covers on this graph
     int stage_arc_cap = 0, stage_pred_cap = 0;  // testing: lower staging limits (0: buffer sizes)
     bool restrict_sweep = false;  // skip chunks out of range for every lane (landmark bounds)
+    bool fused_emit = false;      // the sweep emits the isochrone edges (no k_emit)
     uint32_t* chunk_lo = nullptr;  // [Q * landmarks] per-chunk bounds (restricted sweep)
     uint32_t* chunk_hi = nullptr;
     uint8_t* skip = nullptr;       // [Q] per batch
@@ -442,6 +447,13 @@ int enqueue(iso_workspace* ws, bool want_dist, bool capturing) {
     sw.stage_arc_cap = ws->stage_arc_cap;
     sw.stage_pred_cap = ws->stage_pred_cap;
     sw.skip = ws->skip;
+    sw.fused_emit = ws->fused_emit ? 1 : 0;
+    sw.emit_off = g->emit_off;
+    sw.emit_ent = g->emit_ent;
+    sw.ecnt = ws->ecnt();
+    sw.ebuf = ws->ebuf;
+    sw.ecap = ws->ecap;
+    sw.sync_n = g->h_level_off[ws->sync_levels];
     if (ws->kernel == 1 && ws->core_levels > 0) ISO_CK(iso_launch_core(sw, K, s));
     if (ws->kernel == 1) ISO_CK(iso_launch_sweep_tma(sw, K, ws->tpv, ws->grid, s));
     else ISO_CK(iso_launch_sweep(sw, K, ws->tpv, ws->grid, s));
@@ -455,7 +467,8 @@ int enqueue(iso_workspace* ws, bool want_dist, bool capturing) {
     em.ecnt = ws->ecnt(); em.ebuf = ws->ebuf; em.n = g->n; em.ecap = ws->ecap;
     // four 256-thread CTAs per SM: half an SM's threads, so that the next
     // batch's upward search (1024 threads per CTA) can be placed beside them
-    ISO_CK(iso_launch_emit(em, K, g->num_sms * 4, s));
+    // (with fused emission the sweep has emitted already)
+    if (!ws->fused_emit) ISO_CK(iso_launch_emit(em, K, g->num_sms * 4, s));
     ISO_CK(record(ws->ev[3], s, capturing));
 
     GatherParams ga{};
@@ -524,7 +537,7 @@ int check_opts(const iso_query_opts* o) {
     if (o->threads_per_vertex < 0 || o->ctas_per_sm < 0 || o->fuse_width < -1 || o->barrier_timeout_ns < 0 ||
         o->debug_barrier_extra < 0 || o->schedule_delay < 0 || o->solo_width < -1 || o->chunk_span < 0 ||
         o->core_vertices < -1 || o->debug_stage_arcs < 0 || o->debug_stage_deps < 0 || o->restrict_sweep < 0 ||
-        o->restrict_sweep > 1) {
+        o->restrict_sweep > 1 || o->fused_emission < 0 || o->fused_emission > 1) {
         iso::set_error("iso_query_opts: negative field");
         return ISO_E_INVAL;
     }
@@ -556,14 +569,74 @@ extern "C" int iso_upload_graph(const iso_ch* ch, const iso_alloc* alloc, void* 
     const size_t n = (size_t)ch->n;
     std::vector<uint32_t> off32(n + 5);  // four spare entries keep 16-byte bulk copies in bounds
     std::vector<int2> arcs;
+    std::vector<int32_t> dsrc;
     int rc = ISO_OK;
     auto free_all = [&]() { for (void* p : g->owned) g->A.put(p, g->stream); g->owned.clear(); };
-    for (size_t i = 0; i <= n; ++i) off32[i] = (uint32_t)ch->down_off[i];
+    // Emission entries for fused emission (Section 5): every input arc except
+    // self-loops is checked at its endpoint of lower level (later in sweep
+    // order), against the other one, which the sweep must have finished by
+    // then.  That holds where a downward arc joins the two (the arc itself, or
+    // the reverse arc of a two-way road); for a one-way arc from the lower to
+    // the higher endpoint without one, a dummy downward arc of length
+    // 0x7FFFFFFF is added, which never lowers a label (a sum with it is at
+    // least kInf) but makes the sweep order the two.
+    std::vector<uint32_t> eoff(n + 1, 0);
+    std::vector<int2> ents;
+    std::vector<std::vector<int32_t>> dummy;  // per vertex: dummy arc sources
+    size_t ndummy = 0;
+    try {
+        for (size_t t = 0; t < n; ++t)
+            for (int64_t a = ch->orig_off[t]; a < ch->orig_off[t + 1]; ++a) {
+                const size_t h = (size_t)ch->orig_head[a];
+                if (h != t) eoff[std::max(t, h) + 1]++;
+            }
+        for (size_t v = 0; v < n; ++v) eoff[v + 1] += eoff[v];
+        ents.resize(std::max<size_t>(eoff[n], 1));
+        {
+            std::vector<uint32_t> fill(eoff.begin(), eoff.end() - 1);
+            for (size_t t = 0; t < n; ++t)
+                for (int64_t a = ch->orig_off[t]; a < ch->orig_off[t + 1]; ++a) {
+                    const size_t h = (size_t)ch->orig_head[a];
+                    if (h == t) continue;
+                    ents[fill[std::max(t, h)]++] = make_int2((int)std::min(t, h), ch->orig_id[a]);
+                }
+        }
+        std::vector<int32_t> mark(n, -1);
+        dummy.resize(n);
+        for (size_t v = 0; v < n; ++v) {
+            for (int64_t a = ch->down_off[v]; a < ch->down_off[v + 1]; ++a) mark[ch->down_src[a]] = (int32_t)v;
+            for (uint32_t e = eoff[v]; e < eoff[v + 1]; ++e) {
+                const int32_t hi = ents[e].x;
+                if (mark[hi] != (int32_t)v) { mark[hi] = (int32_t)v; dummy[v].push_back(hi); ++ndummy; }
+            }
+        }
+        // downward CSR with the dummy arcs after each vertex's own
+        const size_t md = ch->down_src.size() + ndummy;
+        if (md > 0xFFFFFFF0u) { free_all(); iso::set_error("iso_upload_graph: too many downward arcs"); return ISO_E_INVAL; }
+        arcs.resize(md + 2);  // two spare entries keep 16-byte loads in bounds
+        dsrc.resize(md);
+        size_t o = 0;
+        for (size_t v = 0; v < n; ++v) {
+            off32[v] = (uint32_t)o;
+            for (int64_t a = ch->down_off[v]; a < ch->down_off[v + 1]; ++a, ++o) {
+                arcs[o] = make_int2(ch->down_src[a], ch->down_w[a]);
+                dsrc[o] = ch->down_src[a];
+            }
+            for (int32_t hi : dummy[v]) { arcs[o] = make_int2(hi, 0x7FFFFFFF); dsrc[o] = hi; ++o; }
+        }
+        off32[n] = (uint32_t)o;
+    } catch (const std::bad_alloc&) {
+        free_all();
+        iso::set_error("iso_upload_graph: out of host memory");
+        return ISO_E_NOMEM;
+    }
+    dummy.clear();
+    dummy.shrink_to_fit();
+    g->dummy_arcs = (int64_t)ndummy;
     for (size_t i = n + 1; i < n + 5; ++i) off32[i] = off32[n];
-    arcs.resize(ch->down_src.size() + 2);  // two spare entries keep 16-byte loads in bounds
-    for (size_t i = 0; i < ch->down_src.size(); ++i) arcs[i] = make_int2(ch->down_src[i], ch->down_w[i]);
     arcs[arcs.size() - 1] = arcs[arcs.size() - 2] = make_int2(0, 0);
-    if ((rc = g->upload(&g->down_off, off32.data(), n + 5)) || (rc = g->upload(&g->down_arc, arcs.data(), arcs.size()))) {
+    if ((rc = g->upload(&g->down_off, off32.data(), n + 5)) || (rc = g->upload(&g->down_arc, arcs.data(), arcs.size())) ||
+        (rc = g->upload(&g->emit_off, eoff.data(), n + 1)) || (rc = g->upload(&g->emit_ent, ents.data(), ents.size()))) {
         free_all(); return rc;
     }
     {
@@ -572,7 +645,7 @@ extern "C" int iso_upload_graph(const iso_ch* ch, const iso_alloc* alloc, void* 
         std::vector<uint2> ca(std::max<uint32_t>(na, 1u), make_uint2(0u, 0u));
         for (int v = 0; v < g->core_cap_n; ++v)
             for (uint32_t a = off32[v]; a < off32[v + 1]; ++a)
-                ca[a] = make_uint2((uint32_t)ch->down_src[a] | ((uint32_t)v << 16), (uint32_t)ch->down_w[a]);
+                ca[a] = make_uint2((uint32_t)arcs[a].x | ((uint32_t)v << 16), (uint32_t)arcs[a].y);
         std::vector<uint32_t> la(ch->level_off.size());
         for (size_t j = 0; j < la.size(); ++j) la[j] = off32[ch->level_off[j]];
         if ((rc = g->upload(&g->core_arc, ca.data(), ca.size())) || (rc = g->upload(&g->level_arc, la.data(), la.size()))) {
@@ -583,7 +656,7 @@ extern "C" int iso_upload_graph(const iso_ch* ch, const iso_alloc* alloc, void* 
     ISO_CK(cudaStreamSynchronize(g->stream));
     try {
         g->h_down_off = off32;
-        g->h_down_src = ch->down_src;
+        g->h_down_src = std::move(dsrc);
         g->h_bfs = ch->bfs;
     } catch (const std::bad_alloc&) {
         free_all();
@@ -672,6 +745,11 @@ extern "C" int iso_workspace_create(iso_graph* g, int32_t lanes, const iso_query
     ws->stage_arc_cap = o.debug_stage_arcs;
     ws->stage_pred_cap = o.debug_stage_deps;
     ws->restrict_sweep = o.restrict_sweep != 0;
+    ws->fused_emit = o.fused_emission != 0;
+    if (ws->fused_emit && ws->kernel != 1) {
+        iso::set_error("iso_workspace_create: fused_emission needs the TMA-staged sweep");
+        return ISO_E_INVAL;
+    }
     if (ws->restrict_sweep && (g->lm.count == 0 || ws->kernel != 1)) {
         iso::set_error("iso_workspace_create: restrict_sweep needs landmarks on the graph (iso_graph_add_landmarks) "
                        "and the TMA-staged sweep");
@@ -1004,7 +1082,7 @@ bool same_config(const iso_workspace* ws, const iso_query_opts& o) {
            ws->solo_width == (o.solo_width < 0 ? 0 : (o.solo_width > 0 ? o.solo_width : kSoloWidth)) &&
            ws->chunk_span == o.chunk_span && ws->core_limit == core_limit_of(o, ws->g->n) &&
            ws->stage_arc_cap == o.debug_stage_arcs && ws->stage_pred_cap == o.debug_stage_deps &&
-           ws->restrict_sweep == (o.restrict_sweep != 0);
+           ws->restrict_sweep == (o.restrict_sweep != 0) && ws->fused_emit == (o.fused_emission != 0);
 }
 }  // namespace
 

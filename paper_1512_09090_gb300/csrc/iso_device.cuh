@@ -103,6 +103,16 @@ struct SweepParams {
     // restricted sweep: skip[q] != 0 = chunk at position q is out of range for
     // every lane (k_skip); its rows are written kInf without gathers (nullable)
     const uint8_t* skip;
+    // fused emission (fused_emit != 0): the input arcs at their later-swept
+    // endpoint v, emit_ent[emit_off[v] .. emit_off[v+1]) = {other endpoint, arc
+    // id}, are emitted by the sweep itself into ebuf / ecnt (as k_emit would)
+    int fused_emit;
+    const uint32_t* emit_off;
+    const int2* emit_ent;
+    int32_t* ecnt;             // [K]
+    int32_t* ebuf;             // [K * ecap]
+    int ecap;
+    int sync_n;                // vertices swept before the chunk schedule (core + leading levels)
 };
 
 // Restricted sweep: which chunks are out of range for every lane of a batch,

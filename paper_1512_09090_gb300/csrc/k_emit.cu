@@ -22,6 +22,7 @@ template <> struct MaskOf<32> { using T = uint32_t; };
 template <> struct MaskOf<64> { using T = unsigned long long; };
 
 constexpr int kEmitThreads = 256;
+constexpr int kEmitBatch = 4;     // rounds of 32 arcs whose loads a warp has in flight together
 constexpr int kSortThreads = 1024;
 constexpr int kSortSmem = 16384;  // ids bucketed in shared memory (64 KB): two sorting CTAs fit an SM
 
@@ -53,7 +54,25 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(EmitParams p) {
         const uint32_t a0 = __shfl_sync(0xffffffffu, my_off, 0);
         const uint32_t a1 = __ldg(p.orig_off + min(u0 + 32, p.n));
         const unsigned long long mu_lane = u < p.n ? (unsigned long long)mask[__ldg(p.tail_of + u)] : 0ull;
-        for (uint32_t base = a0; base < a1; base += 32) {
+        // kEmitBatch rounds of 32 arcs at a time: all their heads, then all the
+        // heads' masks are in flight together (two dependent round trips for up
+        // to 32 * kEmitBatch arcs instead of two per 32)
+        for (uint32_t base0 = a0; base0 < a1; base0 += 32 * kEmitBatch) {
+            unsigned long long mh[kEmitBatch];
+            {
+                int32_t hd[kEmitBatch];
+#pragma unroll
+                for (int r = 0; r < kEmitBatch; ++r) {
+                    const uint32_t a = base0 + 32 * r + lane;
+                    hd[r] = a < a1 ? __ldg(p.orig_head + a) : -1;
+                }
+#pragma unroll
+                for (int r = 0; r < kEmitBatch; ++r) mh[r] = hd[r] >= 0 ? (unsigned long long)mask[hd[r]] : 0ull;
+            }
+#pragma unroll
+            for (int r = 0; r < kEmitBatch; ++r) {
+            const uint32_t base = base0 + 32 * r;
+            if (base >= a1) break;  // warp-uniform
             const uint32_t a = base + lane;
             unsigned long long x = 0;
             int id = 0;
@@ -66,7 +85,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(EmitParams p) {
             }
             const unsigned long long mu = __shfl_sync(0xffffffffu, mu_lane, lo);
             if (a < a1) {
-                x = (mu ^ (unsigned long long)mask[__ldg(p.orig_head + a)]) & kLanes;
+                x = (mu ^ mh[r]) & kLanes;
                 if (x) id = __ldg(p.orig_id + a);
             }
             if (!__any_sync(0xffffffffu, x != 0)) continue;
@@ -83,6 +102,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(EmitParams p) {
                     const int q = at + __popc(b & lt);
                     if (q < p.ecap) p.ebuf[(size_t)i * p.ecap + q] = id;
                 }
+            }
             }
         }
     }

@@ -468,6 +468,56 @@ __device__ void core_rows(const SweepParams& p, int warp, int lane) {
     }
 }
 
+// Fused emission (Section 5: isochrone edges found by a second look at the
+// arcs of a vertex once its label is final).  Input arc e = (a, b) is checked
+// at its later-swept endpoint v against the other one, h, which is final
+// because a downward arc h -> v (a real or a dummy one) makes v's chunk wait
+// for h: e is an isochrone edge for lane i iff bit i of mask[v] XOR mask[h]
+// is set.  `nv` vertices per warp (a power of two <= 32), lane l taking
+// vertex l / (32 / nv) and every (32 / nv)-th of its entries; per lane the
+// ids are appended with one atomicAdd per warp, as in k_emit.  v's mask was
+// written by this warp (ordered by __syncwarp) or before a grid barrier.
+template <int K>
+__device__ void emit_vertices(const SweepParams& p, int v_first, int v_stride, int nv, int v_end, int lane) {
+    using MaskT = typename MaskOf<K>::T;
+    constexpr unsigned long long kLanes = K >= 64 ? ~0ull : ((1ull << K) - 1ull);
+    const MaskT* mask = static_cast<const MaskT*>(p.mask);
+    const int lpv = 32 / nv;
+    const int j = lane / lpv, o = lane % lpv;
+    const int v = v_first + j * v_stride;
+    const bool valid = v < v_end;
+    const uint32_t e0 = valid ? __ldg(p.emit_off + v) : 0u, e1 = valid ? __ldg(p.emit_off + v + 1) : 0u;
+    const unsigned long long mv = valid ? (unsigned long long)__ldcg(mask + v) : 0ull;
+    const unsigned lt = (1u << lane) - 1u;
+    // rounds over the entries, as many as the vertex with the most needs
+    const int rounds = __reduce_max_sync(0xffffffffu, valid ? (int)((e1 - e0 + lpv - 1) / lpv) : 0);
+    for (int r = 0; r < rounds; ++r) {
+        const uint32_t e = e0 + o + (uint32_t)r * lpv;
+        unsigned long long x = 0;
+        int id = 0;
+        if (e < e1) {
+            const int2 en = __ldg(p.emit_ent + e);
+            x = (mv ^ (unsigned long long)__ldcg(mask + en.x)) & kLanes;
+            id = en.y;
+        }
+        unsigned long long todo = __reduce_or_sync(0xffffffffu, (unsigned)x) |
+                                  ((unsigned long long)__reduce_or_sync(0xffffffffu, (unsigned)(x >> 32)) << 32);
+        while (todo) {
+            const int i = __ffsll((long long)todo) - 1;
+            todo &= todo - 1;
+            const unsigned b = __ballot_sync(0xffffffffu, (x >> i) & 1ull);
+            const int leader = __ffs(b) - 1;
+            int at = 0;
+            if (lane == leader) at = atomicAdd(p.ecnt + i, __popc(b));
+            at = __shfl_sync(0xffffffffu, at, leader);
+            if ((x >> i) & 1ull) {
+                const int q = at + __popc(b & lt);
+                if (q < p.ecap) p.ebuf[(size_t)i * p.ecap + q] = id;
+            }
+        }
+    }
+}
+
 // Grid-wide barrier of the whole CTA (the launch is cooperative, so every CTA
 // is resident): an arrival counter that the last arriver resets before it
 // advances a generation word the others poll.  (A barrier on one ever-growing
@@ -597,7 +647,9 @@ __device__ __forceinline__ void release_chunk(const SweepParams& p, Smem& sm, in
     }
 }
 
-template <int K, int TPV>
+// FUSED: the instantiation with fused emission (a separate one, so that the
+// plain kernel's code is not shaped by the emission paths).
+template <int K, int TPV, bool FUSED>
 __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_sweep_tma(SweepParams p) {
     constexpr int VPB = rounds_of<TPV>() * (kConsumers / TPV);
     static_assert(VPB + 5 <= kOffCap, "offset buffer");
@@ -659,6 +711,11 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_sweep_tma(SweepPa
         }
         if (!ok) return;  // the same in every thread of the CTA
     }
+    // fused emission of the vertices swept so far (complete after the last
+    // grid barrier), a warp per 32 of them
+    if constexpr (FUSED)
+        for (int v0 = ((int)blockIdx.x * (kThreads / 32) + warp) * 32; v0 < p.sync_n; v0 += (int)gridDim.x * kThreads)
+            emit_vertices<K>(p, v0, 1, 32, p.sync_n, lane);
 
     if (warp == kConsumers / 32) {
         // ---------------- producer warp ----------------
@@ -804,8 +861,27 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_sweep_tma(SweepPa
         // move on before this warp releases the buffer) and the ready flag
         mbar_wait(&sm.full[stage], (uint32_t)(t / kStages) & 1u, p);
         __threadfence_block();
+        if constexpr (!FUSED) {
+            process_chunk<K, TPV>(p, sm, stage, warp, tid);
+            release_chunk(p, sm, stage, sm.meta[stage].q, sm.meta[stage].level, lane);
+        } else {
+        const Meta mt = sm.meta[stage];  // the buffer may be refilled once released
         process_chunk<K, TPV>(p, sm, stage, warp, tid);
-        release_chunk(p, sm, stage, sm.meta[stage].q, sm.meta[stage].level, lane);
+        release_chunk(p, sm, stage, mt.q, mt.level, lane);
+        // fused emission of this warp's vertices of the chunk, after the chunk
+        // is published, so that no dependent waits for it
+        {
+            if (mt.flags & 4) {  // skipped: a thread per vertex
+                for (int v = mt.v0 + warp * 32; v < mt.v1; v += kConsumers) emit_vertices<K>(p, v, 1, 32, mt.v1, lane);
+            } else if (mt.flags & 2) {  // a warp per vertex
+                emit_vertices<K>(p, mt.v0 + warp, 1, 1, mt.v1, lane);
+            } else {
+#pragma unroll 1
+                for (int r = 0; r < rounds_of<TPV>(); ++r)
+                    emit_vertices<K>(p, mt.v0 + r * (kConsumers / TPV) + warp * (32 / TPV), 1, 32 / TPV, mt.v1, lane);
+            }
+        }
+        }
         done_bits |= 1u << pick;
         while (done_bits & 1u) { done_bits >>= 1; ++base; }
     }
@@ -817,10 +893,10 @@ __global__ void __launch_bounds__(kThreads, 1024 / kThreads) k_sweep_tma(SweepPa
 // gathers in flight (a larger carve-out measurably slowed the chunk phase).
 constexpr size_t kSmemBytes = sizeof(Smem);
 
-template <int K, int TPV>
+template <int K, int TPV, bool FUSED>
 cudaError_t launch(const SweepParams& p, int grid, cudaStream_t s) {
     static std::atomic<unsigned long long> attr{0};
-    if (cudaError_t e = iso_smem_attr_once(k_sweep_tma<K, TPV>, (int)kSmemBytes, attr)) return e;
+    if (cudaError_t e = iso_smem_attr_once(k_sweep_tma<K, TPV, FUSED>, (int)kSmemBytes, attr)) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kThreads);
@@ -831,15 +907,15 @@ cudaError_t launch(const SweepParams& p, int grid, cudaStream_t s) {
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_sweep_tma<K, TPV>, p);
+    return cudaLaunchKernelEx(&cfg, k_sweep_tma<K, TPV, FUSED>, p);
 }
 
 template <int K, int TPV>
 int occupancy() {
     static std::atomic<unsigned long long> attr{0};
-    if (iso_smem_attr_once(k_sweep_tma<K, TPV>, (int)kSmemBytes, attr) != cudaSuccess) return 0;
+    if (iso_smem_attr_once(k_sweep_tma<K, TPV, false>, (int)kSmemBytes, attr) != cudaSuccess) return 0;
     int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_sweep_tma<K, TPV>, kThreads, kSmemBytes) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_sweep_tma<K, TPV, false>, kThreads, kSmemBytes) !=
         cudaSuccess)
         return 0;
     return blocks;
@@ -862,7 +938,8 @@ bool iso_sweep_tma_supported(int K, int tpv) {
 }
 
 cudaError_t iso_launch_sweep_tma(const isod::SweepParams& p, int K, int tpv, int grid, cudaStream_t s) {
-#define X(k, t) if (K == k && tpv == t) return launch<k, t>(p, grid, s);
+#define X(k, t) \
+    if (K == k && tpv == t) return p.fused_emit ? launch<k, t, true>(p, grid, s) : launch<k, t, false>(p, grid, s);
     ISO_TMA_CASES(X)
 #undef X
     return cudaErrorInvalidValue;

@@ -76,6 +76,16 @@ def test_fullsize_vertices_in_range(big):
     assert np.array_equal(got, o_dist != 0x7FFFFFFF)
 
 
+def test_fullsize_fused_emission(big):
+    # the sweep emits the isochrone edges itself, 64 lanes, every lane checked
+    g, dg = big
+    k = 64
+    srcs = synth.draw_sources(g, k, 10_007)
+    taus = synth.draw_taus_uniform(k, 3600, 72000, 20_007)
+    off, arcs, _ = _batch(dg, srcs, taus, fused_emission=1)
+    _against_oracle(g, srcs, taus, off, arcs, list(range(k)))
+
+
 def test_fullsize_16_sources_shared_limit_against_oracle(big):
     # 16 sources batched in one sweep with a shared limit of 36,000
     g, dg = big

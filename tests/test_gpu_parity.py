@@ -43,14 +43,15 @@ def check_batch(g, dg, srcs, taus, want_dist=True, **opts):
     return off, arcs
 
 
-def test_golden_hand_cases(golden_cases):
+@pytest.mark.parametrize("fused", [0, 1])
+def test_golden_hand_cases(golden_cases, fused):
     for case in golden_cases:
         n, t, h, w = arcs_of(case)
         ch = P.iso_build_ch(n, t, h, w)
         dg = P.iso_upload_graph(ch)
         srcs = np.array([q["s"] for q in case["queries"]], np.int32)
         taus = np.array([q["tau"] for q in case["queries"]], np.int32)
-        off, arcs, dist = P.iso_query(dg, srcs, taus, want_dist=True)
+        off, arcs, dist = P.iso_query(dg, srcs, taus, want_dist=True, fused_emission=fused)
         for i, q in enumerate(case["queries"]):
             assert arcs[off[i]:off[i + 1]].tolist() == q["expected"], (case["name"], q)
             if "dist" in q:
@@ -60,6 +61,8 @@ def test_golden_hand_cases(golden_cases):
 
 @pytest.mark.parametrize("seed", range(12))
 def test_random_small_graphs(seed):
+    # random multigraphs: one-way arcs (dummy downward arcs for fused emission),
+    # zero lengths, self-loops, parallel arcs
     rng = np.random.default_rng(100 + seed)
     n = int(rng.integers(1, 60))
     g = synth.random_graph(n, int(rng.integers(0, 5 * n)), wmin=0, wmax=40, seed=seed)
@@ -68,6 +71,43 @@ def test_random_small_graphs(seed):
     srcs = rng.integers(0, n, size=k).astype(np.int32)
     taus = rng.integers(0, 200, size=k).astype(np.int32)
     check_batch(g, dg, srcs, taus)
+    check_batch(g, dg, srcs, taus, fused_emission=1)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_fused_emission_one_way_grid(seed):
+    # a 300 x 300 grid with 30% of its arcs dropped: many one-way arcs, so
+    # dummy downward arcs order their endpoints, through the chunk schedule as
+    # well as the core
+    rng = np.random.default_rng(300 + seed)
+    base = synth.grid_road_graph(300, 300, seed=40 + seed)
+    keep = rng.random(base.m) > 0.3
+    g = synth.RoadGraph(n=base.n, tail=base.tail[keep], head=base.head[keep], weight=base.weight[keep])
+    dg = P.iso_upload_graph(P.iso_build_ch(g.n, g.tail, g.head, g.weight))
+    srcs = synth.draw_sources(g, 16, 50 + seed)
+    taus = synth.draw_taus_uniform(16, 0, 20000, 60 + seed)
+    for core in (0, -1):
+        check_batch(g, dg, srcs, taus, fused_emission=1, core_vertices=core)
+
+
+@pytest.mark.parametrize("k", [1, 5, 16, 64])
+@pytest.mark.parametrize("opts", [{}, {"core_vertices": -1}, {"fuse_width": -1}, {"threads_per_vertex": 0}])
+def test_fused_emission_grid1k(k, opts):
+    g, dg = dev_graph("grid1k")
+    srcs = synth.draw_sources(g, k, 180 + k)
+    taus = synth.draw_taus_uniform(k, 0, 60000, 181 + k)
+    check_batch(g, dg, srcs, taus, want_dist=False, fused_emission=1, use_cuda_graph=1, **opts)
+
+
+def test_fused_emission_with_restricted_sweep_and_overflow():
+    g, dg = lm_graph("grid1k")
+    srcs = synth.draw_sources(g, 3, 191)
+    taus = np.array([2000, 5000, 40000], np.int32)
+    check_batch(g, dg, srcs, taus, fused_emission=1, restrict_sweep=1)
+    # 64 lanes with a large limit
+    srcs = synth.draw_sources(g, 64, 192)
+    taus = np.full(64, 60000, np.int32)
+    check_batch(g, dg, srcs, taus, want_dist=False, fused_emission=1)
 
 
 @pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 8, 16, 17, 32, 64, 65, 130])
