@@ -320,6 +320,7 @@ def main():
     ap.add_argument("--delay", type=int, default=0, help="schedule delay (TMA sweep)")
     ap.add_argument("--solo", type=int, default=0, help="top levels swept by CTA 0 alone: size limit (-1 = none)")
     ap.add_argument("--span", type=int, default=0, help="largest BFS-rank span of a sweep chunk (0 = no limit)")
+    ap.add_argument("--core", type=int, default=0, help="vertices of the per-lane core (0 = automatic, -1 = none)")
     ap.add_argument("--landmarks", type=int, default=8, help="landmarks for restricted sweeps (0 = none)")
     ap.add_argument("--restrict", type=int, default=-1, help="restricted sweep: 1 on, 0 off, -1 autotuned")
     ap.add_argument("--fused", type=int, default=-1, help="fused emission: 1 on, 0 off, -1 autotuned")
@@ -376,7 +377,8 @@ def main():
                 opts[key] = tuned[key]
     for flag, key in ((args.tpv, "threads_per_vertex"), (args.delay, "schedule_delay"),
                       (args.sweep_kernel, "sweep_kernel"), (args.fuse, "fuse_width"),
-                      (args.ctas_per_sm, "ctas_per_sm"), (args.solo, "solo_width"), (args.span, "chunk_span")):
+                      (args.ctas_per_sm, "ctas_per_sm"), (args.solo, "solo_width"), (args.span, "chunk_span"),
+                      (args.core, "core_vertices")):
         if flag:
             opts[key] = flag
     if args.restrict >= 0:
