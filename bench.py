@@ -52,7 +52,11 @@ WORKLOADS = {
 # from one ncu capture per workload, with the hash of the sweep's sources and
 # the sweep options that capture ran; reported as the roofline's traffic only
 # while both match the run (else null).
-SWEEP_TRAFFIC = {}
+SWEEP_TRAFFIC = {
+    # k_sweep_tma<64, 8> on the 18M graph, one launch (ncu, --clock-control none, one pass):
+    # 14,094,586,368 bytes read + 3,376,537,088 written
+    "grid18m_k64": ("b2ee130f3957ab02", {"core_vertices": 20000}, 17471123456),
+}
 SWEEP_SOURCES = ("k_sweep_tma.cu", "iso_device.cuh", "schedule.cpp")
 # sweep options that change the kernel's memory traffic, with their defaults
 # (0 = the library's automatic choice)
@@ -543,6 +547,7 @@ def main():
             "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": kern,
             "alg_bytes_per_launch": alg, "alg_bytes_design": alg_design,
             "traffic_over_alg": None if traffic is None else round(traffic / alg, 3),
+            "traffic_kernel": None if traffic is None else f"k_sweep_tma<{K}> (k_core's own bytes not counted)",
             "peak_source": src, "sweep_ms": round(sw, 4), "lanes_per_launch": K}
     lat = sorted(pipelined["latency_ms"])
     line = {"metric": METRIC, "value": round(value, 2), "unit": "queries/s", "n_gpus": world, "steps": args.steps,
