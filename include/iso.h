@@ -140,9 +140,11 @@ void iso_free_graph(iso_graph* g);
  * max over landmarks L of (d(L,v) - d(L,s), d(s,L) - d(v,L)) -- a lower bound
  * on d(s,v) by the triangle inequality -- exceeds the query's limit for every
  * vertex v of the chunk.  Device memory: 8 * count * n bytes.  Calling it again
- * replaces the landmarks for workspaces created afterwards.  Errors:
- * ISO_E_INVAL (count outside 1..ISO_MAX_LANDMARKS, another hierarchy),
- * ISO_E_NOMEM, ISO_E_CUDA. */
+ * replaces the landmarks; it is refused with ISO_E_INVAL while a workspace
+ * created with restrict_sweep exists (such a workspace keeps using the current
+ * ones; iso_query's own workspaces are dropped and made again).  Errors:
+ * ISO_E_INVAL (count outside 1..ISO_MAX_LANDMARKS, another hierarchy,
+ * restricted workspaces alive), ISO_E_NOMEM, ISO_E_CUDA. */
 #define ISO_MAX_LANDMARKS 16
 int iso_graph_add_landmarks(iso_graph* g, const iso_ch* ch, int32_t count);
 /* The same landmarks and distances on the host (no device needed): vertices[i]

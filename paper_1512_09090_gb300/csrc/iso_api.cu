@@ -139,6 +139,7 @@ struct iso_graph {
     LandmarkSet lm;
     uint32_t* lm_fwd = nullptr;
     uint32_t* lm_bwd = nullptr;
+    std::atomic<int> restricted_ws{0};  // live workspaces with restricted sweeps (they use lm_*)
     int32_t* perm = nullptr;
     int32_t* pos = nullptr;
     int32_t* level_off = nullptr;
@@ -816,6 +817,7 @@ extern "C" int iso_workspace_create(iso_graph* g, int32_t lanes, const iso_query
         iso::set_error("iso_workspace_create: initialisation failed");
         return fail(ISO_E_CUDA);
     }
+    if (ws->restrict_sweep) ++g->restricted_ws;
     *out = ws.release();
     return ISO_OK;
 }
@@ -830,6 +832,7 @@ extern "C" void iso_free_workspace(iso_workspace* ws) {
     for (void* p : ws->owned) ws->g->A.put(p, ws->stream);
     if (ws->h_io) cudaFreeHost(ws->h_io);
     if (ws->h_ctl) cudaFreeHost(ws->h_ctl);
+    if (ws->restrict_sweep) --ws->g->restricted_ws;
     delete ws;
 }
 
@@ -1041,6 +1044,16 @@ extern "C" int iso_graph_add_landmarks(iso_graph* g, const iso_ch* ch, int32_t c
         return ISO_E_INVAL;
     }
     std::lock_guard<std::mutex> lock(g->mu);
+    // workspaces with restricted sweeps hold per-chunk bounds of the current
+    // landmarks and use their device arrays (also from captured CUDA graphs):
+    // iso_query's own are dropped, a caller's must be freed first
+    for (auto*& w : g->query_ws)
+        if (w && w->restrict_sweep) { iso_free_workspace(w); w = nullptr; }
+    if (g->restricted_ws.load() > 0) {
+        iso::set_error("iso_graph_add_landmarks: %d workspaces with restricted sweeps still use the landmarks; "
+                       "free them first", g->restricted_ws.load());
+        return ISO_E_INVAL;
+    }
     LandmarkSet lm;
     try {
         if (iso_landmarks_compute(*ch, count, &lm) != 0) { iso::set_error("iso_graph_add_landmarks: bad input"); return ISO_E_INVAL; }

@@ -452,6 +452,31 @@ def lm_graph(name):
     return _LM[name]
 
 
+def test_landmarks_replaced_only_without_restricted_workspaces():
+    # a workspace with restricted sweeps keeps using the landmarks it was made
+    # with (its chunk bounds, its captured CUDA graph): replacing them is refused
+    # while it lives and allowed once it is freed; iso_query's own restricted
+    # workspace is dropped and made again
+    g, ch = workload("grid1k")
+    dg = P.iso_upload_graph(ch)
+    dg.add_landmarks(ch, 4)
+    srcs = synth.draw_sources(g, 3, 195)
+    taus = np.array([2000, 5000, 9000], np.int32)
+    check_batch(g, dg, srcs, taus, restrict_sweep=1)
+    ws = P.Workspace(dg, 3, restrict_sweep=1, use_cuda_graph=1)
+    with pytest.raises(P.IsoError) as e:
+        dg.add_landmarks(ch, 8)
+    assert e.value.code == P.ISO_E_INVAL
+    ws.submit(srcs, taus)
+    off, arcs, _ = ws.collect()
+    o_off, o_arcs, _ = oracle.query_batch(g.n, g.tail, g.head, g.weight, srcs, taus, threads=8)
+    assert np.array_equal(off, o_off) and np.array_equal(arcs, o_arcs)
+    ws.free()
+    dg.add_landmarks(ch, 8)
+    check_batch(g, dg, srcs, taus, restrict_sweep=1)
+    dg.free()
+
+
 @pytest.mark.parametrize("k,tmax", [(1, 3000), (1, 20000), (3, 8000), (16, 5000), (64, 60000)])
 def test_restricted_sweep(k, tmax):
     # chunks that landmark bounds show out of range for every lane are skipped;
