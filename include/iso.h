@@ -131,7 +131,7 @@ typedef struct {
  * cudaMalloc/cudaFree are used.  The iso_ch may be freed
  * afterwards.  Errors: ISO_E_INVAL, ISO_E_NOMEM, ISO_E_CUDA, ISO_E_NODEV. */
 int iso_upload_graph(const iso_ch* ch, const iso_alloc* alloc, void* stream, iso_graph** out);
-void iso_free_graph(iso_graph* g);
+void iso_free_graph(iso_graph* g);  /* after every workspace created on g (iso_free_workspace) */
 
 /* Landmarks for restricted sweeps: picks `count` far-apart vertices and stores,
  * on the device, every vertex's distance from and to each of them (two PHAST
@@ -289,6 +289,9 @@ typedef struct {
 int iso_workspace_sweep_info(const iso_workspace* ws, iso_sweep_info* out);
 /* Chunks the last collected batch skipped (restricted sweep; 0 otherwise). */
 int iso_workspace_skipped_chunks(const iso_workspace* ws, int64_t* out);
+/* Waits for the workspace's stream and frees its device buffers (into the
+ * graph's allocator).  Free every workspace before the graph it was created
+ * on: iso_free_graph frees only the workspaces iso_query made for itself. */
 void iso_free_workspace(iso_workspace* ws);
 
 /* ---------------------------------------------------------------------------
