@@ -1,7 +1,8 @@
 """Host logic of the continuous-batching server (serving.py) on CPU, with fake
 workspaces in place of device ones: requests are answered by batches of at
 most `lanes`, every request receives its own answer, a failing batch fails
-exactly its requests, and close() ends the workers."""
+exactly its requests, close() ends the workers, and the pool grows only
+while (fake) device memory has room for another workspace."""
 
 import threading
 import time
@@ -79,3 +80,62 @@ def test_close_ends_the_workers():
     srv.close()
     assert all(not t.is_alive() for t in srv._threads)
     assert threading.active_count() >= 1
+
+
+class FakeDevWorkspace(FakeWorkspace):
+    """A fake workspace made the way the server makes device ones: it takes
+    device memory from a fake pool, is warmed by a batch, and accepts `after`
+    (batches chained to the previous batch's sweep)."""
+    pool = None
+
+    def __init__(self, g, lanes, **opts):
+        super().__init__(delay_s=0.02)
+        FakeDevWorkspace.pool["free"] -= FakeDevWorkspace.pool["size"]
+        FakeDevWorkspace.pool["made"] += 1
+
+    def submit(self, sources, taus, after=None):
+        super().submit(sources, taus)
+
+    def free(self):
+        FakeDevWorkspace.pool["free"] += FakeDevWorkspace.pool["size"]
+
+
+@pytest.fixture
+def fake_device(monkeypatch):
+    torch = pytest.importorskip("torch")
+    pool = {"free": 0, "size": 1 << 30, "made": 0}
+    FakeDevWorkspace.pool = pool
+    monkeypatch.setattr(serving._lib, "Workspace", FakeDevWorkspace)
+    monkeypatch.setattr(torch.cuda, "mem_get_info", lambda *a: (pool["free"], 1 << 40))
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a: None)
+    return pool
+
+
+def _flood(srv, n):
+    reqs = [srv.submit(i, 5) for i in range(n)]
+    for i, r in enumerate(reqs):
+        assert r.result(timeout=60).arcs.tolist() == [i, i + 5]
+
+
+def test_pool_grows_while_device_memory_allows(fake_device):
+    # requests wait behind the one busy workspace: the pool grows (up to
+    # max_workspaces), each new workspace warmed before it takes requests
+    fake_device["free"] = 100 << 30
+    with serving.IsoServer(object(), lanes=4, workspaces=1, max_workspaces=3) as srv:
+        assert srv.bytes_per_workspace == 1 << 30      # measured from the first workspace
+        _flood(srv, 200)
+        assert srv.grown >= 1 and srv.refused_growth == 0
+        assert len(srv.workspaces) == 1 + srv.grown <= 3
+    assert fake_device["made"] == 1 + srv.grown
+
+
+def test_growth_refused_when_device_memory_is_short(fake_device):
+    # room for the first workspace only: after it, half of the free memory
+    # (0.25 GB) does not cover another (1 GB), so every growth is refused and
+    # the one workspace answers everything
+    fake_device["free"] = (3 << 30) // 2
+    with serving.IsoServer(object(), lanes=4, workspaces=1, max_workspaces=3, memory_fraction=0.5) as srv:
+        _flood(srv, 120)
+        assert srv.grown == 0 and srv.refused_growth >= 1
+        assert len(srv.workspaces) == 1
+    assert fake_device["made"] == 1
