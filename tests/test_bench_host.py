@@ -1,6 +1,7 @@
 """Host-side checks of bench.py: the reference arm (the oracle on host cores)
 prints one JSON line with the fields the measurement contract asks for, and
-the algorithmic byte count of a sweep follows its definition."""
+the algorithmic byte count of a sweep follows its definition, and the clock
+record (median and maximum SM clock, throttle reasons) is parsed as sampled."""
 
 import json
 import os
@@ -71,3 +72,27 @@ def test_traffic_only_for_the_captured_sources_and_options():
     finally:
         bench.SWEEP_TRAFFIC.clear()
         bench.SWEEP_TRAFFIC.update(saved)
+
+
+def test_clock_summary_parses_samples_and_throttle_reasons(tmp_path):
+    # nvidia-smi --format=csv,noheader,nounits lines as the sampler records them:
+    # index, clocks.sm, clocks.max.sm, power.draw, active reasons, then the four
+    # reasons the bench reports (hw_slowdown, hw_thermal, sw_thermal, sw_power_cap)
+    import bench
+    path = tmp_path / "clocks.csv"
+    path.write_text("\n".join([
+        "0, 2070, 2070, 880.10, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1390.00, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 901.55, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+        "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ]) + "\n")
+    cs = bench.ClockSampler(0)
+    cs.path = str(path)
+    cs.proc = object()          # as if nvidia-smi had been started
+    s = cs.summary()
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    path.write_text("0, 1200, 2070, 500, 0x48, Active, Not Active, Active, Not Active\n")
+    assert cs.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    cs.proc = None              # nvidia-smi missing: no record
+    assert cs.summary() is None
