@@ -580,7 +580,9 @@ extern "C" int iso_ch_info(const iso_ch* ch, iso_ch_stats* out) {
 }
 
 extern "C" int32_t iso_ch_sweep_position(const iso_ch* ch, int32_t v) {
-    if (!ch || v < 0 || v >= ch->n) return -1;
+    iso::clear_error();
+    if (!ch) { iso::set_error("iso_ch_sweep_position: NULL hierarchy"); return -1; }
+    if (v < 0 || v >= ch->n) { iso::set_error("iso_ch_sweep_position: vertex %d outside 0..%d", v, ch->n - 1); return -1; }
     return ch->pos[v];
 }
 

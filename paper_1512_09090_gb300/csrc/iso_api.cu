@@ -1075,7 +1075,8 @@ extern "C" int iso_graph_add_landmarks(iso_graph* g, const iso_ch* ch, int32_t c
 }
 
 extern "C" int iso_workspace_timings(const iso_workspace* ws, float* ms4) {
-    if (!ws || !ms4) return ISO_E_INVAL;
+    iso::clear_error();
+    if (!ws || !ms4) { iso::set_error("iso_workspace_timings: NULL argument"); return ISO_E_INVAL; }
     std::memcpy(ms4, ws->phase_ms, sizeof(ws->phase_ms));
     return ISO_OK;
 }

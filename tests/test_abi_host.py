@@ -165,3 +165,38 @@ def test_query_without_device_fails_loudly():
     rc = lib().iso_upload_graph(ch.handle, None, None, ctypes.byref(out))
     assert rc == P.ISO_E_NODEV
     assert not out.value
+
+
+def test_every_entry_point_rejects_null_handles():
+    # no device needed: each call with NULL handles returns its error (or -1)
+    # and sets its own message; the free calls accept NULL
+    N = None
+    calls = {
+        "iso_build_ch": ((3, 0, N, N, N, N, N), P.ISO_E_INVAL),
+        "iso_ch_info": ((N, N), P.ISO_E_INVAL),
+        "iso_ch_view_arrays": ((N, N), P.ISO_E_INVAL),
+        "iso_ch_sweep_position": ((N, 0), -1),
+        "iso_save_ch": ((N, b"unused.ch"), P.ISO_E_INVAL),
+        "iso_load_ch": ((N, N), P.ISO_E_INVAL),
+        "iso_ch_landmarks": ((N, 8, N, N, N), P.ISO_E_INVAL),
+        "iso_upload_graph": ((N, N, N, N), P.ISO_E_INVAL),
+        "iso_graph_add_landmarks": ((N, N, 8), P.ISO_E_INVAL),
+        "iso_query": ((N, 1, N, N, N, N, 0, N, N, N), P.ISO_E_INVAL),
+        "iso_query_noalloc": ((N, 1, N, N, N, N, 0, N), P.ISO_E_INVAL),
+        "iso_workspace_create": ((N, 64, N, N, N), P.ISO_E_INVAL),
+        "iso_submit": ((N, 1, N, N, 0, N), P.ISO_E_INVAL),
+        "iso_submit_after": ((N, N, 1, N, N, 0, N), P.ISO_E_INVAL),
+        "iso_collect": ((N, N, N, 0, N), P.ISO_E_INVAL),
+        "iso_collect_range": ((N, N, 0), P.ISO_E_INVAL),
+        "iso_workspace_trace": ((N, N, N, 0), -1),
+        "iso_workspace_timings": ((N, N), P.ISO_E_INVAL),
+        "iso_workspace_sweep_info": ((N, N), P.ISO_E_INVAL),
+        "iso_workspace_skipped_chunks": ((N, N), P.ISO_E_INVAL),
+    }
+    L = lib()
+    for name, (args, want) in calls.items():
+        assert getattr(L, name)(*args) == want, name
+        msg = L.iso_last_error().decode()
+        assert msg.startswith(name), (name, msg)
+    for name in ("iso_free_ch", "iso_free_graph", "iso_free_workspace"):
+        getattr(L, name)(None)
